@@ -1,0 +1,130 @@
+"""Planted mistakes: each test compiles a copy of the oracle's C source with one
+plausible error and checks that the pins of ``test_oracle_pins.py`` reject it.
+
+This shows the pins are discriminating: a dropped term, a wrong sign, a wrong
+index or weight, a conjugate on the wrong operand, a wrong denominator or a
+misread scaling exponent each fail at least one independent check.  The
+mistakes are planted on the CPU, in the oracle only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from test_oracle_pins import _brute, _rel
+
+MUTATIONS = {
+    "weights_all_one": ("return omega == 0 ? 1.0 : 2.0;", "return 1.0;"),
+    "dc_doubled": ("return omega == 0 ? 1.0 : 2.0;", "return 2.0;"),
+    "nyquist_kept": ("return (m - 1) / 2 + 1;", "return m / 2 + 1;"),
+    "dft_sign": ("im -= d * sin(theta);", "im += d * sin(theta);"),
+    "conj_on_first": ("zi += wt * (xi * yr - xr * yi);", "zi += wt * (xr * yi - xi * yr);"),
+    "dropped_term": ("zr += wt * (xr * yr + xi * yi);", "zr += wt * (xr * yr);"),
+    "sigma_over_m": ("sigma[v] = sqrt(s / (double)(m - 1));", "sigma[v] = sqrt(s / (double)m);"),
+    "scaling_exponent_sign": ("return pow(sigma, -alpha);", "return pow(sigma, alpha);"),
+    "norm_over_m": ("return 1.0 / (ORACLE_PI * (double)(m - 1));",
+                    "return 1.0 / (ORACLE_PI * (double)m);"),
+    "mean_over_m_minus_1": ("ref[v] = s / (double)m;", "ref[v] = s / (double)(m - 1);"),
+    "dft_index_shift": ("long r = ((long)w * (long)j) % (long)m;",
+                        "long r = ((long)w * (long)(j + 1)) % (long)m;"),
+    "user_ref_ignored": ("for (int v = 0; v < n1; ++v) r1[v] = (double)ref1[v];",
+                         "for (int v = 0; v < n1; ++v) r1[v] = 0.0;"),
+    "interp_weight": ("double t = (x - xa) / (xb - xa);", "double t = (x - xa) / (xb - x0);"),
+    "psi_unscaled": ("psi[(long)r * n2 + b] = f * zi;", "psi[(long)r * n2 + b] = norm * zi;"),
+}
+
+
+def _battery():
+    """Run the independent pins; return the names of those that fail."""
+    failed = []
+
+    def check(name, fn):
+        try:
+            if not fn():
+                failed.append(name)
+        except Exception:  # a mutant may also trip an argument check
+            failed.append(name)
+
+    y1 = workloads.random_stack(6, 5, seed=1, offset=0.5)
+    y2 = workloads.random_stack(6, 4, seed=2, offset=-1.0)
+    y3 = workloads.random_stack(5, 4, seed=3)
+
+    def brute_homo():
+        p, q, _, _ = oracle.corr2d(y1, alpha=0.5)
+        bp, bq = _brute(y1, alpha=0.5)
+        return _rel(p, bp) < 1e-12 and np.abs(q - bq).max() <= 1e-12 * np.abs(bp).max()
+
+    def brute_hetero_odd():
+        p, q, _, _ = oracle.corr2d(y3, workloads.random_stack(5, 3, seed=9))
+        bp, bq = _brute(y3, workloads.random_stack(5, 3, seed=9))
+        return _rel(p, bp) < 1e-12 and _rel(q, bq) < 1e-12
+
+    def brute_user_ref():
+        p, q, _, _ = oracle.corr2d(y1, y2, ref1=y1[0], ref2=y2[-1], alpha=1.0)
+        bp, bq = _brute(y1, y2, ref1=y1[0], ref2=y2[-1], alpha=1.0)
+        return _rel(p, bp) < 1e-12 and _rel(q, bq) < 1e-12
+
+    def parseval_even():
+        m = 8
+        a = workloads.random_stack(m, 6, seed=4)
+        p, _, _, _ = oracle.corr2d(a)
+        d = a.astype(np.float64) - a.astype(np.float64).mean(0)
+        alt = (-1.0) ** np.arange(m)
+        rhs = m * d.T @ d - np.outer(alt @ d, alt @ d)
+        return _rel(math.pi * (m - 1) * p, rhs) < 1e-12
+
+    def pearson_diag():
+        p, _, _, _ = oracle.corr2d(workloads.random_stack(9, 5, seed=5), alpha=1.0)
+        return np.allclose(np.diag(p), 9 / math.pi, rtol=1e-12)
+
+    def closed_form():
+        m, n = 8, 32
+        y, c, g, a = workloads.sinusoid_bands(m, n, [0.0, 50.0], seed=6)
+        p, q, _, _ = oracle.corr2d(y)
+        nu = np.arange(n, dtype=np.float64)
+        L = 1.0 / (1.0 + ((nu[None, :] - c[:, None]) / g[:, None]) ** 2)
+        E = ((a[:, None] * L) * np.exp(1j * np.deg2rad([0.0, 50.0]))[:, None]).sum(0)
+        Z = (m * m / 2.0) * np.outer(E, np.conj(E)) / (math.pi * (m - 1))
+        return _rel(p, Z.real) < 1e-5 and np.abs(q - Z.imag).max() < 1e-5 * np.abs(Z).max()
+
+    def dft_numpy():
+        d = np.random.default_rng(7).standard_normal((9, 4))
+        return np.abs(oracle.dft(d) - np.fft.fft(d, axis=0)[:5].T).max() < 1e-12
+
+    def sigma_numpy():
+        a = workloads.random_stack(7, 5, seed=8, offset=1.0)
+        d = oracle.dynamic(a, oracle.reference_mean(a))
+        return np.allclose(oracle.sigma(d), a.astype(np.float64).std(0, ddof=1), rtol=1e-12)
+
+    def interp_numpy():
+        x = workloads.jittered_axis(40, 0.0, 29.0, np.random.default_rng(1))
+        yy = workloads.random_stack(2, 40, seed=2)
+        out, _ = oracle.interp_linear(x, yy, 30)
+        g = np.linspace(0.0, 29.0, 30)
+        return all(np.allclose(out[j], np.interp(g, x, yy[j].astype(np.float64)), atol=1e-12)
+                   for j in range(2))
+
+    for name, fn in [("brute_homo", brute_homo), ("brute_hetero_odd", brute_hetero_odd),
+                     ("brute_user_ref", brute_user_ref), ("parseval_even", parseval_even),
+                     ("pearson_diag", pearson_diag), ("closed_form", closed_form),
+                     ("dft_numpy", dft_numpy), ("sigma_numpy", sigma_numpy),
+                     ("interp_numpy", interp_numpy)]:
+        check(name, fn)
+    return failed
+
+
+def test_unmutated_oracle_passes_battery():
+    assert _battery() == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = oracle.source()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    lib = oracle.compile_source(src.replace(old, new), str(tmp_path / f"mut_{name}.so"))
+    with oracle.use_library(lib):
+        failed = _battery()
+    assert failed, f"planted mistake {name} passed every pin"

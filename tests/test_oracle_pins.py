@@ -1,0 +1,404 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by mathematics.
+
+Nothing here re-types the oracle's own formulas: each check uses a second,
+independent route (a time-domain kernel, numpy's FFT, Parseval's identity, a
+closed form for sinusoidal bands, an exact invariance, the Noda sign rules or
+the R index expression of the paper's FFT snippet).  A dropped term, a wrong
+sign or index, a transposed operand or a wrong weight in the oracle fails at
+least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _furanmale():
+    rows = []
+    with open(os.path.join(GOLDEN, "furanmale_excerpt.txt")) as f:
+        for line in f:
+            if line.startswith("#") or line.startswith("nu"):
+                continue
+            vals = line.split()
+            if vals:
+                rows.append([float(v) for v in vals[1:]])
+    return np.array(rows, dtype=np.float32)
+
+
+def _brute(y1, y2=None, ref1=None, ref2=None, alpha=0.0, norm=None):
+    """Time-domain evaluation of the half-spectrum correlation.
+
+    With d = y - ref, summing w_omega e^{i 2 pi omega (k - j)/m} over the kept
+    frequencies gives, for each pair of perturbation steps (j, k), the kernels
+      c(j,k) = 1 + 2 sum_{omega=1}^{K} cos(2 pi omega (k - j)/m)
+      s(j,k) =     2 sum_{omega=1}^{K} sin(2 pi omega (k - j)/m)
+    and Phi + i Psi = norm * sum_{j,k} d1(j) d2(k) (c + i s).  No DFT is formed.
+    """
+    y1 = y1.astype(np.float64)
+    m, n1 = y1.shape
+    homo = y2 is None
+    y2 = y1 if homo else y2.astype(np.float64)
+    n2 = y2.shape[1]
+    r1 = y1.mean(axis=0) if ref1 is None else np.asarray(ref1, np.float64)
+    if homo:
+        r2 = r1
+    else:
+        r2 = y2.mean(axis=0) if ref2 is None else np.asarray(ref2, np.float64)
+    d1 = y1 - r1
+    d2 = y2 - r2
+    K = (m - 1) // 2
+    c = np.empty((m, m))
+    s = np.empty((m, m))
+    for j in range(m):
+        for k in range(m):
+            cc, ss = 1.0, 0.0
+            for w in range(1, K + 1):
+                ang = 2.0 * math.pi * w * (k - j) / m
+                cc += 2.0 * math.cos(ang)
+                ss += 2.0 * math.sin(ang)
+            c[j, k], s[j, k] = cc, ss
+    if norm is None:
+        norm = 1.0 / (math.pi * (m - 1))
+    phi = np.zeros((n1, n2))
+    psi = np.zeros((n1, n2))
+    for a in range(n1):
+        for b in range(n2):
+            pr = pi = 0.0
+            for j in range(m):
+                for k in range(m):
+                    pr += d1[j, a] * d2[k, b] * c[j, k]
+                    pi += d1[j, a] * d2[k, b] * s[j, k]
+            phi[a, b] = norm * pr
+            psi[a, b] = norm * pi
+    if alpha > 0:
+        sd1 = np.sqrt((d1 ** 2).sum(axis=0) / (m - 1))
+        sd2 = np.sqrt((d2 ** 2).sum(axis=0) / (m - 1))
+        f = np.outer(sd1 ** -alpha, sd2 ** -alpha)
+        phi, psi = phi * f, psi * f
+    return phi, psi
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+# ---------------------------------------------------------------- frequencies
+
+@pytest.mark.parametrize("m", range(2, 14))
+def test_kept_frequencies_follow_r_index_expression(m):
+    """Sec. 4.2 FFT snippet: fft(x)[1:(NROW - 1) %/% 2 + 1] (R precedence: ':' first).
+
+    The snippet picks frequencies with repetition; the product with Conj() then
+    sums every pick, so the pick count is the weight.  For even m that count is
+    the weight exactly.  For odd m the expression picks the top bin K = (m-1)/2
+    once, while the text (every omega != 0 used twice) and the Hermitian pairing
+    of K with m-K (Eq. symmeFT) count it twice; the text's reading is taken."""
+    idx_1based = [(k // 2) + 1 for k in range(1, m)]  # (1:(m-1)) %/% 2 + 1
+    counts = {}
+    for i in idx_1based:
+        counts[i - 1] = counts.get(i - 1, 0) + 1
+    K = (m - 1) // 2
+    assert sorted(counts) == list(range(oracle.num_freq(m)))
+    for omega, cnt in counts.items():
+        if m % 2 == 1 and omega == K and K > 0:
+            assert cnt == 1 and oracle.weight(omega) == 2.0
+        else:
+            assert oracle.weight(omega) == cnt
+    if m % 2 == 0:
+        assert m // 2 not in counts  # Nyquist bin never used
+
+
+# ----------------------------------------------------------------------- DFT
+
+@pytest.mark.parametrize("m", [2, 3, 5, 8, 11, 16, 31, 64])
+def test_dft_is_numpy_fft_truncated(m):
+    rng = np.random.default_rng(m)
+    d = rng.standard_normal((m, 7))
+    Y = oracle.dft(d)
+    ref = np.fft.fft(d, axis=0)[: (m - 1) // 2 + 1].T
+    assert np.max(np.abs(Y - ref)) < 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_reference_and_sigma_match_numpy():
+    y = workloads.random_stack(9, 13, seed=3, offset=2.0)
+    ref = oracle.reference_mean(y)
+    assert np.allclose(ref, y.astype(np.float64).mean(axis=0), rtol=0, atol=1e-14)
+    d = oracle.dynamic(y, ref)
+    assert np.array_equal(d, y.astype(np.float64) - ref)
+    assert np.allclose(oracle.sigma(d), y.astype(np.float64).std(axis=0, ddof=1), rtol=1e-13)
+
+
+# ------------------------------------------------------------- brute force
+
+@pytest.mark.parametrize("m,n1,n2", [(2, 3, 3), (3, 4, 4), (4, 5, 3), (5, 6, 6), (8, 4, 5),
+                                     (9, 8, 8)])
+def test_brute_force_time_domain(m, n1, n2):
+    y1 = workloads.random_stack(m, n1, seed=10 + m, offset=0.5)
+    phi, psi, _, _ = oracle.corr2d(y1)
+    bphi, bpsi = _brute(y1)
+    assert np.max(np.abs(phi - bphi)) < 1e-13 * max(1, np.abs(bphi).max())
+    assert np.max(np.abs(psi - bpsi)) < 1e-13 * max(1, np.abs(bphi).max())
+    y2 = workloads.random_stack(m, n2, seed=20 + m, offset=-1.0)
+    phi, psi, _, _ = oracle.corr2d(y1, y2, alpha=0.5)
+    bphi, bpsi = _brute(y1, y2, alpha=0.5)
+    assert _rel(phi, bphi) < 1e-13 and np.max(np.abs(psi - bpsi)) <= 1e-13 * np.abs(bphi).max()
+
+
+def test_brute_force_user_reference_and_norm():
+    y1 = workloads.random_stack(7, 5, seed=4)
+    y2 = workloads.random_stack(7, 6, seed=5)
+    ref1, ref2 = y1[0].copy(), y2[-1].copy()  # first / last spectrum as reference
+    phi, psi, s1, s2 = oracle.corr2d(y1, y2, ref1=ref1, ref2=ref2, norm=0.25, alpha=1.0)
+    bphi, bpsi = _brute(y1, y2, ref1=ref1, ref2=ref2, norm=0.25, alpha=1.0)
+    assert _rel(phi, bphi) < 1e-13 and _rel(psi, bpsi) < 1e-13
+    # Eq. stdev with the chosen reference, not re-centred on the mean
+    assert np.allclose(s1, np.sqrt(((y1.astype(np.float64) - ref1.astype(np.float64)) ** 2).sum(0) / 6), rtol=1e-13)
+
+
+def test_brute_force_paper_excerpt():
+    """Real data printed in the paper (FuranMale, 6 temperatures x 5 wavenumbers)."""
+    y = _furanmale()
+    assert y.shape == (6, 5)
+    phi, psi, _, _ = oracle.corr2d(y)
+    bphi, bpsi = _brute(y)
+    assert _rel(phi, bphi) < 1e-12
+    assert np.max(np.abs(psi - bpsi)) < 1e-12 * np.abs(bphi).max()
+    assert np.all(np.diag(phi) > 0)
+
+
+# ---------------------------------------------------------------- Parseval
+
+@pytest.mark.parametrize("m", [3, 4, 7, 10, 33, 64])
+def test_parseval_links_frequency_sum_to_covariance(m):
+    """sum over all m bins of Y1 conj(Y2) = m sum_j d1 d2; pairing bins omega and m-omega
+    (Eq. symmeFT) leaves pi (m-1) Phi = m sum_j d1 d2 - [m even] Y1(m/2) Y2(m/2)."""
+    y1 = workloads.random_stack(m, 11, seed=m)
+    y2 = workloads.random_stack(m, 9, seed=m + 1, offset=3.0)
+    phi, _, _, _ = oracle.corr2d(y1, y2)
+    d1 = y1.astype(np.float64) - y1.astype(np.float64).mean(0)
+    d2 = y2.astype(np.float64) - y2.astype(np.float64).mean(0)
+    rhs = m * d1.T @ d2
+    if m % 2 == 0:
+        alt = (-1.0) ** np.arange(m)
+        rhs -= np.outer(alt @ d1, alt @ d2)
+    assert _rel(math.pi * (m - 1) * phi, rhs) < 1e-12
+
+
+@pytest.mark.parametrize("m", [5, 9, 15])
+def test_odd_m_ft_equals_ht_synchronous_up_to_m_over_pi(m):
+    """Sec. 2: FT and HT give the same spectra; exactly Phi_FT = (m/pi) Phi_HT for odd m."""
+    y = workloads.random_stack(m, 6, seed=m)
+    phi, _, _, _ = oracle.corr2d(y)
+    d = oracle.dynamic(y, oracle.reference_mean(y))
+    hphi, _ = oracle.hilbert_noda(d, d)
+    assert _rel(phi, (m / math.pi) * hphi) < 1e-12
+
+
+def test_pearson_diagonal_is_m_over_pi_for_odd_m():
+    m = 13
+    y = workloads.random_stack(m, 10, seed=1, offset=5.0)
+    phi, psi, _, _ = oracle.corr2d(y, alpha=1.0)
+    assert np.allclose(np.diag(phi), m / math.pi, rtol=1e-12)
+    assert np.allclose(np.diag(psi), 0.0, atol=1e-12)
+
+
+# ------------------------------------------------------------- closed form
+
+@pytest.mark.parametrize("m", [3, 8, 11, 64])
+def test_closed_form_sinusoidal_bands(m):
+    """t_j = j/m, y = sum_b L_b(nu) a_b sin(2 pi t + phi_b): only bin 1 is non-zero,
+    Y_b(1) = a_b m e^{i phi_b}/(2i), so Phi + i Psi = norm (m^2/2) sum_bc L_b L_c a_b a_c
+    e^{i (phi_b - phi_c)}."""
+    n = 64
+    phases = [0.0, 30.0, 60.0, 90.0]
+    y, c, g, a = workloads.sinusoid_bands(m, n, phases, seed=7)
+    phi, psi, _, _ = oracle.corr2d(y)
+    nu = np.arange(n, dtype=np.float64)
+    L = 1.0 / (1.0 + ((nu[None, :] - c[:, None]) / g[:, None]) ** 2)  # bands x n
+    ph = np.deg2rad(phases)
+    E = (a[:, None] * L) * np.exp(1j * ph)[:, None]  # bands x n
+    Z = (m * m / 2.0) * (E.sum(0)[:, None] * np.conj(E.sum(0))[None, :])
+    Z /= math.pi * (m - 1)
+    # inputs are rounded to FP32, so agreement is at FP32 level
+    assert _rel(phi, Z.real) < 3e-6
+    assert np.max(np.abs(psi - Z.imag)) < 3e-6 * np.abs(Z).max()
+
+
+def test_fig1_cases_pure_sync_and_pure_async():
+    """Fig. 1 (a): identical response -> Psi = 0; (b) pi/2 lag -> Phi = 0 (Sec. 2)."""
+    m = 16
+    t = np.arange(m) / m
+    s0 = np.sin(2 * np.pi * t)
+    s90 = np.sin(2 * np.pi * t + np.pi / 2)
+    y = np.stack([s0, s0, s90], axis=1).astype(np.float32)
+    phi, psi, _, _ = oracle.corr2d(y)
+    scale = abs(phi[0, 0])
+    assert abs(psi[0, 1]) < 1e-7 * scale and phi[0, 1] > 0
+    assert abs(phi[0, 2]) < 1e-7 * scale
+    # column 2 leads column 0 by 90 deg: Psi(2, 0) > 0 (Noda rule 3)
+    assert psi[2, 0] > 0.99 * scale and psi[0, 2] < 0
+
+
+# --------------------------------------------------------------- invariants
+
+def test_homo_symmetry_and_autopeaks():
+    y = workloads.c1()
+    phi, psi, _, _ = oracle.corr2d(y)
+    assert np.array_equal(phi, phi.T)
+    assert np.array_equal(psi, -psi.T)
+    assert np.all(np.diag(psi) == 0.0)
+    assert np.all(np.diag(phi) >= 0.0)
+
+
+def _quantised(m, n, seed):
+    """Values on a 2^-10 grid in [-4, 4): adding 8 stays exact in FP32."""
+    rng = np.random.default_rng(seed)
+    return (rng.integers(-4096, 4096, (m, n)) / 1024.0).astype(np.float32)
+
+
+def test_baseline_offset_invariance():
+    y = _quantised(12, 9, seed=2)
+    base = np.float32(8.0) + np.arange(9, dtype=np.float32)  # per-variable constant
+    p0, q0, _, _ = oracle.corr2d(y)
+    p1, q1, _, _ = oracle.corr2d(y + base)
+    assert _rel(p1, p0) < 1e-13 and np.max(np.abs(q1 - q0)) < 1e-13 * np.abs(p0).max()
+
+
+@pytest.mark.parametrize("m,shift", [(10, 3), (11, 4)])
+def test_circular_shift_invariance(m, shift):
+    y = workloads.random_stack(m, 8, seed=m)
+    p0, q0, _, _ = oracle.corr2d(y)
+    p1, q1, _, _ = oracle.corr2d(np.roll(y, shift, axis=0))
+    assert _rel(p1, p0) < 1e-12 and np.max(np.abs(q1 - q0)) < 1e-12 * np.abs(p0).max()
+
+
+def test_time_reversal_flips_async_sign():
+    y = workloads.random_stack(9, 8, seed=9)
+    p0, q0, _, _ = oracle.corr2d(y)
+    p1, q1, _, _ = oracle.corr2d(y[::-1].copy())
+    assert _rel(p1, p0) < 1e-12 and _rel(q1, -q0) < 1e-12
+
+
+def test_hetero_swap_and_self_hetero_equals_homo():
+    y1 = workloads.random_stack(10, 7, seed=1)
+    y2 = workloads.random_stack(10, 5, seed=2)
+    p12, q12, _, _ = oracle.corr2d(y1, y2)
+    p21, q21, _, _ = oracle.corr2d(y2, y1)
+    assert _rel(p21, p12.T) < 1e-13 and _rel(q21, -q12.T) < 1e-13
+    ph, qh, _, _ = oracle.corr2d(y1)
+    ps, qs, _, _ = oracle.corr2d(y1, y1.copy())
+    assert np.array_equal(ph, ps) and np.array_equal(qh, qs)
+
+
+def test_amplitude_scaling():
+    y = _quantised(8, 6, seed=5)
+    p0, q0, _, _ = oracle.corr2d(y)
+    p1, q1, _, _ = oracle.corr2d(y * np.float32(4.0))
+    assert _rel(p1, 16 * p0) < 1e-14 and _rel(q1, 16 * q0) < 1e-14
+    # Pearson scaling removes the amplitude (Eq. pearsonsyn)
+    p2, q2, _, _ = oracle.corr2d(y, alpha=1.0)
+    p3, q3, _, _ = oracle.corr2d(y * np.float32(4.0), alpha=1.0)
+    assert _rel(p3, p2) < 1e-13 and _rel(q3, q2) < 1e-13
+    # Pareto (alpha = 0.5) leaves a factor c^2 / c
+    p4, _, _, _ = oracle.corr2d(y, alpha=0.5)
+    p5, _, _, _ = oracle.corr2d(y * np.float32(4.0), alpha=0.5)
+    assert _rel(p5, 4 * p4) < 1e-13
+
+
+def test_norm_override_and_constant_variable():
+    y = workloads.random_stack(6, 5, seed=8)
+    y[:, 2] = 3.25  # constant variable: sigma = 0
+    p0, q0, s, _ = oracle.corr2d(y)
+    p1, _, _, _ = oracle.corr2d(y, norm=1.0)
+    assert _rel(p1, p0 * math.pi * 5) < 1e-13
+    assert s[2] == 0.0
+    p2, q2, _, _ = oracle.corr2d(y, alpha=0.5)
+    assert np.all(p2[2, :] == 0) and np.all(p2[:, 2] == 0) and np.all(q2[2, :] == 0)
+    assert np.all(np.isfinite(p2))
+
+
+def test_row_subset_matches_full():
+    y = workloads.random_stack(10, 40, seed=3)
+    p, q, _, _ = oracle.corr2d(y)
+    rows = np.array([0, 5, 17, 39], np.int32)
+    ps, qs, _, _ = oracle.corr2d(y, rows=rows, nthreads=2)
+    assert np.array_equal(ps, p[rows]) and np.array_equal(qs, q[rows])
+
+
+def test_invalid_arguments_rejected():
+    with pytest.raises(ValueError):
+        oracle.corr2d(np.zeros((1, 4), np.float32))  # m < 2: Norm divides by m - 1
+    with pytest.raises(ValueError):
+        oracle.corr2d(np.zeros((3, 4), np.float32), np.zeros((4, 4), np.float32))
+
+
+# ---------------------------------------------------------- Noda sign rules
+
+def test_noda_sign_rules_on_phase_lagged_bands():
+    """Sec. 3 rules 1-4 on the 0/30/60 deg three-band input: at band centres
+    sign(Phi) = sign(cos(dphi)) and sign(Psi(nu_b, nu_c)) = sign(sin(phi_b - phi_c))."""
+    y, c, g, a = workloads.sinusoid_bands(11, 500, [0.0, 30.0, 60.0], seed=0, noise=0.01,
+                                          centers=[100.0, 250.0, 400.0], widths=[8, 8, 8])
+    phi, psi, _, _ = oracle.corr2d(y)
+    ph = np.deg2rad([0.0, 30.0, 60.0])
+    idx = [100, 250, 400]
+    for b in range(3):
+        for cc in range(3):
+            if b == cc:
+                continue
+            assert np.sign(phi[idx[b], idx[cc]]) == np.sign(math.cos(ph[b] - ph[cc]))
+            assert np.sign(psi[idx[b], idx[cc]]) == np.sign(math.sin(ph[b] - ph[cc]))
+
+
+def test_hilbert_noda_async_sign_agrees_with_ft():
+    """Eq. HilbNoda: antisymmetric matrix -> homo Psi_HT antisymmetric; its sign pattern
+    on lagged bands matches the FT approach (rule 3)."""
+    y, c, g, a = workloads.sinusoid_bands(32, 60, [0.0, 45.0], seed=1,
+                                          centers=[15.0, 45.0], widths=[4, 4])
+    d = oracle.dynamic(y, oracle.reference_mean(y))
+    hphi, hpsi = oracle.hilbert_noda(d, d)
+    assert np.max(np.abs(hpsi + hpsi.T)) < 1e-13 * np.abs(hphi).max()
+    _, psi, _, _ = oracle.corr2d(y)
+    assert np.sign(hpsi[45, 15]) == np.sign(psi[45, 15]) == 1.0
+
+
+# ------------------------------------------------------------ interpolation
+
+def test_interp_matches_numpy_interp_and_endpoints():
+    rng = np.random.default_rng(0)
+    x = workloads.jittered_axis(130, 0.0, 99.0, rng)
+    y = workloads.random_stack(4, 130, seed=1)
+    out, dyn = oracle.interp_linear(x, y, 100, ref=np.zeros(100, np.float32))
+    grid = np.linspace(0.0, 99.0, 100)
+    for j in range(4):
+        assert np.allclose(out[j], np.interp(grid, x, y[j].astype(np.float64)), rtol=0,
+                           atol=1e-12)
+    assert np.array_equal(out[:, 0], y[:, 0].astype(np.float64))
+    assert np.array_equal(out[:, -1], y[:, -1].astype(np.float64))
+    assert np.array_equal(dyn, out)
+
+
+def test_interp_reproduces_linear_functions_and_subtracts_reference():
+    rng = np.random.default_rng(3)
+    x = workloads.jittered_axis(50, -2.0, 7.0, rng)
+    y = np.stack([1.5 + 0.25 * x, -3.0 * x]).astype(np.float32)
+    out, _ = oracle.interp_linear(x.astype(np.float64), y.astype(np.float64).astype(np.float32), 37)
+    grid = np.linspace(-2.0, 7.0, 37)
+    # FP32 inputs: linear up to the rounding of the knots
+    assert np.allclose(out[0], 1.5 + 0.25 * grid, atol=5e-6)
+    assert np.allclose(out[1], -3.0 * grid, atol=5e-5)
+    ref = np.linspace(0, 1, 37).astype(np.float32)
+    out2, dyn = oracle.interp_linear(x, y, 37, ref=ref)
+    assert np.array_equal(dyn, out2 - ref.astype(np.float64))
+
+
+def test_interp_rejects_non_increasing_axis():
+    x = np.array([0.0, 1.0, 1.0, 2.0])
+    with pytest.raises(ValueError):
+        oracle.interp_linear(x, np.zeros((2, 4), np.float32), 3)
