@@ -1,0 +1,194 @@
+/*
+ * corr2d.h -- C ABI of the GB300 (sm_103a) implementation of generalized
+ * two-dimensional correlation analysis (Geitner et al., arXiv:1808.00685,
+ * the corr2D R package).
+ *
+ * The library computes, for one or two stacks of m spectra sampled along a
+ * shared perturbation axis, the synchronous (Phi) and asynchronous (Psi)
+ * correlation spectra:
+ *
+ *   1. reference spectrum and dynamic spectra          (Eqs. ref, dynspec)
+ *   2. DFT along the perturbation axis, half spectrum   (Eqs. disFT, symmeFT)
+ *   3. Phi + i Psi = Norm sum_w w_w Y1 conj(Y2)          (Eq. disint2d, Sec. 4.2)
+ *   4. optional scaling by (sigma1 sigma2)^-alpha       (Eqs. stdev, scalesyn,
+ *                                                        scaleasyn)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Stacks are row-major FP32 matrices, m rows (row j = perturbation step t_j)
+ *   by n columns (spectral variables nu), leading dimension ld >= n elements:
+ *   the layout of the paper's input matrix (Sec. 3, "m perturbation values by
+ *   rows and n spectral values by columns").
+ * - Outputs Phi and Psi are row-major FP32 n1 x n2 matrices with leading
+ *   dimension ldo (elements): row = nu1 of stack 1, column = nu2 of stack 2
+ *   (Sec. 4.2: FT matrix built with byrow = TRUE over the columns of ft1).
+ * - Every pointer argument that names device memory must point to memory of
+ *   the context's device (cudaMalloc, torch CUDA tensors); host pointers are
+ *   only accepted where a comment says "host".  The caller owns all input and
+ *   output buffers; the library keeps no pointer after a call returns.
+ * - Work is enqueued on the context's CUDA stream and the call returns before
+ *   the GPU finishes.  Results are valid once the stream has been
+ *   synchronised; corr2d_synchronize() does that and also reports device-side
+ *   wait time-outs.
+ * - No function throws or aborts.  Each returns a corr2d_status; on failure
+ *   corr2d_last_error() describes the first problem found.  Arguments are
+ *   validated before anything is launched, so a rejected call leaves outputs
+ *   untouched.
+ * - Half-spectrum weights (Sec. 4.2 and Eq. symmeFT): omega = 0 .. K with
+ *   K = floor((m-1)/2), weight 1 for omega = 0 and 2 otherwise; for even m the
+ *   Nyquist bin m/2 is not used.
+ */
+#ifndef CORR2D_H
+#define CORR2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CORR2D_OK = 0,
+  CORR2D_EINVAL = 1,       /* bad shape, pointer, alignment or parameter */
+  CORR2D_ENOMEM = 2,       /* device workspace could not be allocated */
+  CORR2D_ECUDA = 3,        /* a CUDA runtime/driver call failed */
+  CORR2D_ETIMEOUT = 4,     /* a device-side wait ran past its limit */
+  CORR2D_EUNSUPPORTED = 5  /* valid request outside what this build supports */
+} corr2d_status;
+
+/* Arithmetic of the DFT and of the cross-spectrum contraction.
+ * Every precision computes the reference mean and the centering subtraction
+ * in FP64 and accumulates in FP32. */
+typedef enum {
+  CORR2D_PREC_FP32 = 0,  /* CUDA-core FP32 FMA (the plain GPU baseline) */
+  CORR2D_PREC_SPLIT = 1, /* tcgen05 FP16 hi/lo split: hi*hi + hi*lo + lo*hi */
+  CORR2D_PREC_BF16 = 2   /* tcgen05 plain BF16 operands */
+} corr2d_precision;
+
+typedef enum {
+  CORR2D_REF_MEAN = 0, /* perturbation-mean reference per stack (Eq. ref) */
+  CORR2D_REF_USER = 1  /* caller-supplied reference spectra ref1/ref2 */
+} corr2d_ref_mode;
+
+/* Homo correlation computes tiles with nu1-block <= nu2-block and writes each
+ * tile and its mirror (Phi symmetric, Psi antisymmetric: Sec. 3 and Sec. 4.3).
+ * This flag forces every tile to be computed instead. */
+#define CORR2D_FLAG_NO_MIRROR 1u
+
+typedef struct {
+  int ref_mode;       /* corr2d_ref_mode */
+  const float* ref1;  /* device, n1 values; used when ref_mode == CORR2D_REF_USER */
+  const float* ref2;  /* device, n2 values; hetero + user reference only */
+  double norm;        /* <= 0 selects the default 1/(pi (m-1)) (Eq. disint2d) */
+  double alpha;       /* 0: no scaling; 1: Pearson; 0.5: Pareto (Eqs. scale*) */
+  int precision;      /* corr2d_precision */
+  unsigned flags;     /* CORR2D_FLAG_* */
+} corr2d_params;
+
+typedef struct corr2d_ctx corr2d_ctx; /* opaque: device, stream, workspace, tuning cache */
+
+/* Fill *p with the defaults: mean reference, default norm, alpha 0, SPLIT. */
+corr2d_status corr2d_params_default(corr2d_params* p);
+
+/* Create a context bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context; the caller releases it with corr2d_destroy. */
+corr2d_status corr2d_create(corr2d_ctx** out, int device, void* cuda_stream);
+
+/* Release a context and its device workspace (synchronises its stream). */
+corr2d_status corr2d_destroy(corr2d_ctx* ctx);
+
+/* Change the stream later calls enqueue on. */
+corr2d_status corr2d_set_stream(corr2d_ctx* ctx, void* cuda_stream);
+
+/* Text of the last failure on this context ("" after success). NULL ctx
+ * gives the last failure of corr2d_create. */
+const char* corr2d_last_error(const corr2d_ctx* ctx);
+
+/* Wait for the context's stream, then report ETIMEOUT if a kernel gave up on
+ * a bounded wait since the previous call, or ECUDA on an asynchronous error. */
+corr2d_status corr2d_synchronize(corr2d_ctx* ctx);
+
+/*
+ * Preprocessing onto a common, equally spaced spectral axis, then reference
+ * subtraction (the interpolation mechanism of Sec. 4.2, applied along the
+ * spectral axis, followed by Eq. dynspec).
+ *   m       rows (perturbation steps) of y_raw, >= 1
+ *   n_raw   raw points per row, >= 2
+ *   x_raw   device, n_raw FP64 positions, strictly increasing and finite;
+ *           a kernel checks this and the next corr2d_synchronize() returns
+ *           EINVAL if it does not hold (the outputs are then meaningless)
+ *   y_raw   device, m x n_raw FP32, leading dimension n_raw
+ *   n_out   points of the target grid x_k = x_0 + k (x_last - x_0)/(n_out - 1),
+ *           last point x_last exactly; >= 2
+ *   y_out   device, m x n_out FP32 (linear interpolation, weights in FP64)
+ *   ref     device, n_out FP32 reference spectrum, or NULL
+ *   dyn_out device, m x n_out FP32 receiving y_out - ref, or NULL
+ */
+corr2d_status corr2d_preprocess(corr2d_ctx* ctx, int m, int n_raw, const double* x_raw,
+                                const float* y_raw, int n_out, float* y_out, const float* ref,
+                                float* dyn_out);
+
+/*
+ * Synchronous and asynchronous correlation spectra of one problem.
+ *   m          perturbation steps shared by both stacks, >= 2 (the
+ *              normalisation divides by m - 1); tensor-core precisions
+ *              accept m <= 512, FP32 accepts m <= 1600 (EUNSUPPORTED beyond)
+ *   y1, ld1    device stack 1, m x n1, ld1 >= n1
+ *   y2, ld2    device stack 2, m x n2, or y2 == NULL for homo correlation
+ *              (stack 2 := stack 1, n2 and ld2 ignored)
+ *   params     NULL for the defaults (corr2d_params_default)
+ *   phi, psi   device outputs, n1 x n2 FP32, leading dimension ldo >= n2;
+ *              tensor-core precisions need ldo % 4 == 0 and 16-byte aligned
+ *              phi/psi (TMA stores), else EINVAL
+ *   sigma1_out, sigma2_out  device, n1 / n2 FP32 standard deviations
+ *              (Eq. stdev with the chosen reference), or NULL
+ * A spectral variable with sigma = 0 and alpha > 0 gets scale factor 0: its
+ * row and column of Phi and Psi are 0 (instead of 0/0).
+ */
+corr2d_status corr2d_compute(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1, int n2,
+                             const float* y2, int ld2, const corr2d_params* params, float* phi,
+                             float* psi, long ldo, float* sigma1_out, float* sigma2_out);
+
+/*
+ * Same computation with every buffer in HOST memory: the library copies the
+ * stacks to its device workspace, computes, and copies Phi and Psi back in
+ * row slabs so that copies overlap the kernels.  Blocks until the results are
+ * in phi/psi.  y2 == NULL selects homo correlation.  Pinned host memory gives
+ * the fastest copies; pageable memory works.
+ */
+corr2d_status corr2d_compute_host(corr2d_ctx* ctx, int m, int n1, const float* y1, int n2,
+                                  const float* y2, const corr2d_params* params, float* phi,
+                                  float* psi, long ldo);
+
+/* One problem of a batch (device pointers, same conventions as
+ * corr2d_compute; y2 == NULL selects homo). */
+typedef struct {
+  int m, n1, n2;
+  const float* y1;
+  const float* y2;
+  float* phi;
+  float* psi;
+  long ldo;
+} corr2d_problem;
+
+/*
+ * Many independent correlations of uneven m, n1, n2: one batched DFT launch
+ * and one persistent cross-spectrum launch over a cost-ordered tile list, with
+ * per-problem tile shapes from the tuner; the launches are captured once in a
+ * CUDA graph per batch layout and replayed.  host_problems is a host array of
+ * `count` descriptors.  shared_params (NULL = defaults) applies to every
+ * problem; its ref_mode must be CORR2D_REF_MEAN and its precision a
+ * tensor-core precision.
+ */
+corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* host_problems,
+                           const corr2d_params* shared_params);
+
+/* Library version string. */
+const char* corr2d_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CORR2D_H */

@@ -1,0 +1,279 @@
+"""Python binding of libcorr2d, the GB300 (sm_103a) generalized 2D correlation library.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI declared in ``include/corr2d.h``.  The functions
+``corr2d_*`` mirror the C entry points one to one (raw pointers and sizes);
+``Context`` wraps them for torch CUDA tensors.  Importing works without a GPU;
+loading the library fails loudly if it has not been built, and there is no
+CPU fallback.
+
+The method: Geitner et al., arXiv:1808.00685 (the corr2D R package) --
+dynamic spectra (Eq. dynspec), DFT along the perturbation axis (Eq. disFT),
+half-spectrum complex correlation Phi + i Psi (Eq. disint2d, Sec. 4.2) and
+optional scaling (Eqs. scalesyn, scaleasyn).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from ._build import build, lib_path
+
+__all__ = [
+    "Corr2dError", "Context", "load", "build", "lib_path", "EXPORTED_SYMBOLS",
+    "PREC_FP32", "PREC_SPLIT", "PREC_BF16", "REF_MEAN", "REF_USER", "FLAG_NO_MIRROR",
+]
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED"}
+PREC_FP32, PREC_SPLIT, PREC_BF16 = 0, 1, 2
+REF_MEAN, REF_USER = 0, 1
+FLAG_NO_MIRROR = 1
+_PREC_BY_NAME = {"fp32": PREC_FP32, "split": PREC_SPLIT, "bf16": PREC_BF16}
+
+EXPORTED_SYMBOLS = (
+    "corr2d_params_default", "corr2d_create", "corr2d_destroy", "corr2d_set_stream",
+    "corr2d_last_error", "corr2d_synchronize", "corr2d_preprocess", "corr2d_compute",
+    "corr2d_compute_host", "corr2d_batch", "corr2d_version",
+)
+
+
+class corr2d_params(ctypes.Structure):
+    _fields_ = [("ref_mode", ctypes.c_int), ("ref1", ctypes.c_void_p), ("ref2", ctypes.c_void_p),
+                ("norm", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("precision", ctypes.c_int), ("flags", ctypes.c_uint)]
+
+
+class corr2d_problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n1", ctypes.c_int), ("n2", ctypes.c_int),
+                ("y1", ctypes.c_void_p), ("y2", ctypes.c_void_p), ("phi", ctypes.c_void_p),
+                ("psi", ctypes.c_void_p), ("ldo", ctypes.c_long)]
+
+
+class Corr2dError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load libcorr2d (built by ``build()``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or lib_path()
+        if not os.path.exists(p):
+            raise RuntimeError(f"libcorr2d is not built ({p}); run paper_1808_00685_gb300.build()")
+        lib = ctypes.CDLL(p)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        sig = {
+            "corr2d_params_default": (i, [ctypes.POINTER(corr2d_params)]),
+            "corr2d_create": (i, [ctypes.POINTER(vp), i, vp]),
+            "corr2d_destroy": (i, [vp]),
+            "corr2d_set_stream": (i, [vp, vp]),
+            "corr2d_last_error": (ctypes.c_char_p, [vp]),
+            "corr2d_synchronize": (i, [vp]),
+            "corr2d_preprocess": (i, [vp, i, i, vp, vp, i, vp, vp, vp]),
+            "corr2d_compute": (i, [vp, i, i, vp, i, i, vp, i, ctypes.POINTER(corr2d_params), vp,
+                                   vp, ctypes.c_long, vp, vp]),
+            "corr2d_compute_host": (i, [vp, i, i, vp, i, vp, ctypes.POINTER(corr2d_params), vp,
+                                        vp, ctypes.c_long]),
+            "corr2d_batch": (i, [vp, i, ctypes.POINTER(corr2d_problem),
+                                 ctypes.POINTER(corr2d_params)]),
+            "corr2d_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _ = d
+        _lib = lib
+        return lib
+
+
+# ------------------------------------------------------------ C-ABI mirrors
+def corr2d_params_default() -> corr2d_params:
+    p = corr2d_params()
+    load().corr2d_params_default(ctypes.byref(p))
+    return p
+
+
+def corr2d_create(device: int = 0, stream: int | None = None) -> int:
+    h = ctypes.c_void_p()
+    st = load().corr2d_create(ctypes.byref(h), device, stream)
+    if st != OK:
+        raise Corr2dError(st, load().corr2d_last_error(None).decode())
+    return h.value
+
+
+def corr2d_last_error(ctx: int | None) -> str:
+    return load().corr2d_last_error(ctx).decode()
+
+
+def _check(ctx, st):
+    if st != OK:
+        raise Corr2dError(st, corr2d_last_error(ctx))
+
+
+def corr2d_destroy(ctx: int) -> None:
+    _check(None, load().corr2d_destroy(ctx))
+
+
+def corr2d_set_stream(ctx: int, stream: int | None) -> None:
+    _check(ctx, load().corr2d_set_stream(ctx, stream))
+
+
+def corr2d_synchronize(ctx: int) -> None:
+    _check(ctx, load().corr2d_synchronize(ctx))
+
+
+def corr2d_preprocess(ctx, m, n_raw, x_raw, y_raw, n_out, y_out, ref=None, dyn_out=None) -> None:
+    _check(ctx, load().corr2d_preprocess(ctx, m, n_raw, x_raw, y_raw, n_out, y_out, ref, dyn_out))
+
+
+def corr2d_compute(ctx, m, n1, y1, ld1, n2, y2, ld2, params, phi, psi, ldo, sigma1=None,
+                   sigma2=None) -> None:
+    pp = ctypes.byref(params) if params is not None else None
+    _check(ctx, load().corr2d_compute(ctx, m, n1, y1, ld1, n2, y2, ld2, pp, phi, psi, ldo,
+                                      sigma1, sigma2))
+
+
+def corr2d_compute_host(ctx, m, n1, y1, n2, y2, params, phi, psi, ldo) -> None:
+    pp = ctypes.byref(params) if params is not None else None
+    _check(ctx, load().corr2d_compute_host(ctx, m, n1, y1, n2, y2, pp, phi, psi, ldo))
+
+
+def corr2d_batch(ctx, problems, params=None) -> None:
+    arr = (corr2d_problem * len(problems))(*problems)
+    pp = ctypes.byref(params) if params is not None else None
+    _check(ctx, load().corr2d_batch(ctx, len(problems), arr, pp))
+
+
+def corr2d_version() -> str:
+    return load().corr2d_version().decode()
+
+
+# ------------------------------------------------------------ torch helpers
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def make_params(precision="split", alpha=0.0, norm=0.0, ref1=None, ref2=None,
+                no_mirror=False) -> corr2d_params:
+    p = corr2d_params_default()
+    p.precision = _PREC_BY_NAME[precision] if isinstance(precision, str) else int(precision)
+    p.alpha = float(alpha)
+    p.norm = float(norm)
+    if ref1 is not None:
+        p.ref_mode = REF_USER
+        p.ref1 = _ptr(ref1)
+        p.ref2 = _ptr(ref2)
+    p.flags = FLAG_NO_MIRROR if no_mirror else 0
+    return p
+
+
+class Context:
+    """A library context on one CUDA device and stream (torch tensors in, out)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        self.handle = corr2d_create(device, stream.cuda_stream)
+
+    def close(self):
+        if self.handle:
+            corr2d_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def synchronize(self):
+        corr2d_synchronize(self.handle)
+
+    @staticmethod
+    def alloc_out(n1, n2, device, ld=None):
+        """Phi/Psi buffers with a leading dimension that suits TMA stores."""
+        import torch
+        ldo = ld or (n2 + 3) // 4 * 4
+        phi = torch.empty((n1, ldo), dtype=torch.float32, device=device)
+        psi = torch.empty((n1, ldo), dtype=torch.float32, device=device)
+        return phi, psi, ldo
+
+    def compute(self, y1, y2=None, precision="split", alpha=0.0, norm=0.0, ref1=None, ref2=None,
+                no_mirror=False, out=None, want_sigma=False):
+        """Phi, Psi (n1 x n2 views) of the m x n1 stack y1 (and y2, or homo)."""
+        import torch
+        assert y1.is_cuda and y1.dtype == torch.float32 and y1.dim() == 2
+        m, n1 = y1.shape
+        if y2 is not None:
+            assert y2.is_cuda and y2.dtype == torch.float32 and y2.shape[0] == m
+        n2 = n1 if y2 is None else y2.shape[1]
+        if out is None:
+            phi, psi, ldo = self.alloc_out(n1, n2, y1.device)
+        else:
+            phi, psi = out
+            ldo = phi.stride(0)
+        s1 = torch.empty(n1, dtype=torch.float32, device=y1.device) if want_sigma else None
+        s2 = (torch.empty(n2, dtype=torch.float32, device=y1.device)
+              if (want_sigma and y2 is not None) else None)
+        params = make_params(precision, alpha, norm, ref1, ref2, no_mirror)
+        corr2d_compute(self.handle, m, n1, _ptr(y1), y1.stride(0), n2, _ptr(y2),
+                       y2.stride(0) if y2 is not None else 0, params, _ptr(phi), _ptr(psi), ldo,
+                       _ptr(s1), _ptr(s2))
+        res = (phi[:, :n2], psi[:, :n2])
+        if want_sigma:
+            return res + (s1, s2 if s2 is not None else s1)
+        return res
+
+    def preprocess(self, x_raw, y_raw, n_out, ref=None):
+        import torch
+        m, n_raw = y_raw.shape
+        out = torch.empty((m, n_out), dtype=torch.float32, device=y_raw.device)
+        dyn = torch.empty_like(out) if ref is not None else None
+        corr2d_preprocess(self.handle, m, n_raw, _ptr(x_raw), _ptr(y_raw), n_out, _ptr(out),
+                          _ptr(ref), _ptr(dyn))
+        return out, dyn
+
+    def batch(self, problems, precision="split", alpha=0.0, norm=0.0, no_mirror=False):
+        """problems: list of (y1, y2 or None, phi, psi) torch tensors (phi/psi n1 x ldo)."""
+        ps = []
+        for y1, y2, phi, psi in problems:
+            m, n1 = y1.shape
+            n2 = n1 if y2 is None else y2.shape[1]
+            ps.append(corr2d_problem(m, n1, n2, _ptr(y1), _ptr(y2), _ptr(phi), _ptr(psi),
+                                     phi.stride(0)))
+        corr2d_batch(self.handle, ps, make_params(precision, alpha, norm, None, None, no_mirror))
+
+    def compute_host(self, y1, y2=None, precision="split", alpha=0.0, norm=0.0, out=None):
+        """Host (CPU) tensors in and out; copies overlap the kernels inside the library."""
+        import torch
+        m, n1 = y1.shape
+        n2 = n1 if y2 is None else y2.shape[1]
+        if out is None:
+            phi = torch.empty((n1, n2), dtype=torch.float32)
+            psi = torch.empty((n1, n2), dtype=torch.float32)
+        else:
+            phi, psi = out
+        params = make_params(precision, alpha, norm)
+        corr2d_compute_host(self.handle, m, n1, _ptr(y1), n2, _ptr(y2), params, _ptr(phi),
+                            _ptr(psi), phi.stride(0))
+        return phi, psi

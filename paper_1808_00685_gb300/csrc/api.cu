@@ -1,0 +1,952 @@
+// C ABI of the library (declared in include/corr2d.h): argument validation,
+// device workspace, twiddle tables, TMA descriptors, tile lists, the tile
+// tuner, batch graphs and the host-buffer path.  All arithmetic of the method
+// runs in the kernels of k_prep.cu, k_xspec.cu, k_simt.cu and k_interp.cu.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "corr2d.h"
+#include "internal.h"
+
+using namespace c2d;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                    const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                    const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Tuned choice for one problem shape.
+struct TileChoice {
+  int bn = 128;
+  int mirror = 1;
+};
+
+struct BatchCache {
+  std::vector<uint8_t> key;   // serialized problem list + params
+  cudaGraphExec_t exec = nullptr;
+  DevBuf desc;                // device descriptors of this batch
+  DevBuf ops;                 // operand rows + scales
+  std::vector<int> bn;        // chosen tile width per problem
+  int grid = 0;
+};
+
+}  // namespace
+
+struct corr2d_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  std::string err;
+  int* d_err = nullptr;
+  unsigned long long limit_ns = 2000000000ull;
+  PFN_encodeTiled encode = nullptr;
+  DevBuf ops;       // operand rows / frequency planes of corr2d_compute
+  DevBuf desc;      // uploaded descriptors of corr2d_compute
+  std::vector<uint8_t> desc_host;  // last uploaded descriptor bytes
+  std::map<std::pair<int, int>, DevBuf> twiddles;  // (m, planes) -> table
+  std::map<int, DevBuf> simt_tw;                    // m -> FP32 cos/sin table
+  std::map<std::tuple<int, int, int, int, int>, TileChoice> tuned;  // shape -> choice
+  BatchCache batch;
+  DevBuf host_in;   // corr2d_compute_host: stacks
+  DevBuf host_out;  // corr2d_compute_host: two slab pairs
+  bool fault_alloc = false;
+};
+
+namespace {
+
+corr2d_status fail(corr2d_ctx* ctx, corr2d_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf; else g_create_error = buf;
+  return st;
+}
+
+#define CUDA_TRY(ctx, call)                                                              \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, CORR2D_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+// Keep the caller's current device; work on the context's device meanwhile.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+corr2d_status ensure(corr2d_ctx* ctx, DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return CORR2D_OK;
+  if (ctx->fault_alloc) return fail(ctx, CORR2D_ENOMEM, "workspace allocation refused (injected)");
+  if (b.p) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  size_t want = bytes < 256 ? 256 : bytes;
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return fail(ctx, CORR2D_ENOMEM, "cannot allocate %zu bytes of device workspace", want);
+  }
+  b.bytes = want;
+  return CORR2D_OK;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Is p device memory usable on `dev`?  (managed memory counts as device)
+bool is_device_ptr(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeDevice) return a.device == dev;
+  return a.type == cudaMemoryTypeManaged;
+}
+
+corr2d_status check_params(corr2d_ctx* ctx, const corr2d_params* p, bool homo) {
+  if (p->ref_mode != CORR2D_REF_MEAN && p->ref_mode != CORR2D_REF_USER)
+    return fail(ctx, CORR2D_EINVAL, "ref_mode %d is not a corr2d_ref_mode", p->ref_mode);
+  if (p->ref_mode == CORR2D_REF_USER) {
+    if (!p->ref1 || (!homo && !p->ref2))
+      return fail(ctx, CORR2D_EINVAL, "user reference mode needs ref1%s", homo ? "" : " and ref2");
+    if (!is_device_ptr(p->ref1, ctx->device) || (!homo && !is_device_ptr(p->ref2, ctx->device)))
+      return fail(ctx, CORR2D_EINVAL, "reference spectra must be device memory");
+  }
+  if (!std::isfinite(p->norm)) return fail(ctx, CORR2D_EINVAL, "norm must be finite");
+  if (!(p->alpha >= 0.0) || !std::isfinite(p->alpha))
+    return fail(ctx, CORR2D_EINVAL, "alpha must be finite and >= 0");
+  if (p->precision < CORR2D_PREC_FP32 || p->precision > CORR2D_PREC_BF16)
+    return fail(ctx, CORR2D_EINVAL, "precision %d is not a corr2d_precision", p->precision);
+  return CORR2D_OK;
+}
+
+// Twiddle table of the tensor-core DFT for (m, planes), built once per context.
+corr2d_status get_twiddles(corr2d_ctx* ctx, int m, int planes, const uint8_t** out) {
+  auto key = std::make_pair(m, planes);
+  auto it = ctx->twiddles.find(key);
+  if (it == ctx->twiddles.end()) {
+    size_t bytes = make_twiddles(m, planes, nullptr);
+    std::vector<uint8_t> host(bytes);
+    make_twiddles(m, planes, host.data());
+    DevBuf b;
+    corr2d_status st = ensure(ctx, b, bytes);
+    if (st != CORR2D_OK) return st;
+    CUDA_TRY(ctx, cudaMemcpy(b.p, host.data(), bytes, cudaMemcpyHostToDevice));
+    it = ctx->twiddles.emplace(key, b).first;
+  }
+  *out = (const uint8_t*)it->second.p;
+  return CORR2D_OK;
+}
+
+corr2d_status get_simt_twiddles(corr2d_ctx* ctx, int m, const float** out) {
+  auto it = ctx->simt_tw.find(m);
+  if (it == ctx->simt_tw.end()) {
+    std::vector<float> host(2 * (size_t)m);
+    for (int r = 0; r < m; ++r) {
+      double th = 2.0 * kPi * (double)r / (double)m;
+      host[2 * r] = (float)std::cos(th);
+      host[2 * r + 1] = (float)std::sin(th);
+    }
+    DevBuf b;
+    corr2d_status st = ensure(ctx, b, host.size() * sizeof(float));
+    if (st != CORR2D_OK) return st;
+    CUDA_TRY(ctx, cudaMemcpy(b.p, host.data(), host.size() * sizeof(float),
+                             cudaMemcpyHostToDevice));
+    it = ctx->simt_tw.emplace(m, b).first;
+  }
+  *out = (const float*)it->second.p;
+  return CORR2D_OK;
+}
+
+corr2d_status encode_operand(corr2d_ctx* ctx, CUtensorMap* tm, const void* base, int rowlen,
+                             int rows, int box_rows, int planes) {
+  cuuint64_t dims[2] = {(cuuint64_t)rowlen, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)rowlen * 2};
+  cuuint32_t box[2] = {CHUNK_ELEMS, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = ctx->encode(tm, planes == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                           : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                           2, const_cast<void*>(base), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, CORR2D_ECUDA, "operand tensor map encode failed (%d)", (int)r);
+  return CORR2D_OK;
+}
+
+corr2d_status encode_output(corr2d_ctx* ctx, CUtensorMap* tm, float* base, int rows, int cols,
+                            long ldo) {
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ldo * 4};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = ctx->encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, CORR2D_ECUDA, "output tensor map encode failed (%d)", (int)r);
+  return CORR2D_OK;
+}
+
+// Tile list of one problem, appended to `items`.
+void append_tiles(std::vector<XItem>& items, int prob, int n1, int n2, int bn, bool mirror,
+                  int ti_begin, int ti_end) {
+  const int nt2 = (n2 + bn - 1) / bn;
+  for (int ti = ti_begin; ti < ti_end; ++ti)
+    for (int tj = mirror ? ti : 0; tj < nt2; ++tj)
+      items.push_back(XItem{prob, (uint16_t)ti, (uint16_t)tj});
+}
+
+// Host descriptor blob: [PrepJob...][PrepItem...][XProblem...][XItem...], each 128-aligned.
+struct Blob {
+  std::vector<uint8_t> bytes;
+  size_t off_jobs = 0, off_pitems = 0, off_probs = 0, off_xitems = 0;
+  int njobs = 0, npitems = 0, nprobs = 0, nxitems = 0;
+};
+
+Blob pack(const std::vector<PrepJob>& jobs, const std::vector<PrepItem>& pitems,
+          const std::vector<XProblem>& probs, const std::vector<XItem>& xitems) {
+  Blob b;
+  size_t off = 0;
+  b.off_jobs = off;
+  off = align_up(off + jobs.size() * sizeof(PrepJob), 128);
+  b.off_pitems = off;
+  off = align_up(off + pitems.size() * sizeof(PrepItem), 128);
+  b.off_probs = off;
+  off = align_up(off + probs.size() * sizeof(XProblem), 128);
+  b.off_xitems = off;
+  off = align_up(off + xitems.size() * sizeof(XItem), 128);
+  b.bytes.assign(off, 0);
+  if (!jobs.empty()) memcpy(b.bytes.data() + b.off_jobs, jobs.data(), jobs.size() * sizeof(PrepJob));
+  if (!pitems.empty())
+    memcpy(b.bytes.data() + b.off_pitems, pitems.data(), pitems.size() * sizeof(PrepItem));
+  if (!probs.empty())
+    memcpy(b.bytes.data() + b.off_probs, probs.data(), probs.size() * sizeof(XProblem));
+  if (!xitems.empty())
+    memcpy(b.bytes.data() + b.off_xitems, xitems.data(), xitems.size() * sizeof(XItem));
+  b.njobs = (int)jobs.size();
+  b.npitems = (int)pitems.size();
+  b.nprobs = (int)probs.size();
+  b.nxitems = (int)xitems.size();
+  return b;
+}
+
+// Upload a descriptor blob unless the device copy already holds these bytes.
+corr2d_status upload_blob(corr2d_ctx* ctx, DevBuf& dev, std::vector<uint8_t>& last,
+                          const Blob& b) {
+  if (dev.p && last == b.bytes) return CORR2D_OK;
+  corr2d_status st = ensure(ctx, dev, b.bytes.size());
+  if (st != CORR2D_OK) return st;
+  CUDA_TRY(ctx, cudaMemcpyAsync(dev.p, b.bytes.data(), b.bytes.size(), cudaMemcpyHostToDevice,
+                                ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // host blob may change after return
+  last = b.bytes;
+  return CORR2D_OK;
+}
+
+struct TcPlan {
+  int planes, kp, nch, rowlen;
+  size_t bytesA, bytesB, off_s1, off_s2, total;
+};
+
+TcPlan plan_tc(int m, int n1, int n2, bool homo, int precision) {
+  TcPlan p;
+  p.planes = precision == CORR2D_PREC_SPLIT ? 2 : 1;
+  p.kp = freq_padded(m, p.planes);
+  p.nch = chunks_for(m, p.planes);
+  p.rowlen = p.nch * CHUNK_ELEMS;
+  p.bytesA = align_up((size_t)n1 * p.rowlen * 2, 1024);
+  p.bytesB = align_up((size_t)n2 * p.rowlen * 2, 1024);
+  p.off_s1 = p.bytesA + p.bytesB;
+  p.off_s2 = p.off_s1 + align_up((size_t)n1 * 4, 256);
+  p.total = p.off_s2 + align_up((size_t)n2 * 4, 256);
+  (void)homo;
+  return p;
+}
+
+// Enqueue the tensor-core path of one problem whose descriptors are built here.
+// rows [ti_begin, ti_end) of 128-row tiles are computed; out_row_tile0 shifts
+// their output rows (host-buffer slabs).  skip_prep reuses operands already in ops.
+corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1, int n2,
+                         const float* y2, int ld2, const corr2d_params& p, float* phi,
+                         float* psi, long ldo, int out_rows, float* sig1, float* sig2,
+                         const TileChoice& tc, int ti_begin, int ti_end, int out_row_tile0,
+                         bool skip_prep, DevBuf& opsbuf, DevBuf& descbuf,
+                         std::vector<uint8_t>& desc_last) {
+  const bool homo = (y2 == nullptr);
+  TcPlan pl = plan_tc(m, n1, n2, homo, p.precision);
+  corr2d_status st = ensure(ctx, opsbuf, pl.total);
+  if (st != CORR2D_OK) return st;
+  const uint8_t* wtab = nullptr;
+  st = get_twiddles(ctx, m, pl.planes, &wtab);
+  if (st != CORR2D_OK) return st;
+  uint8_t* ops = (uint8_t*)opsbuf.p;
+  uint16_t* opA = (uint16_t*)ops;
+  uint16_t* opB = (uint16_t*)(ops + pl.bytesA);
+  float* s1 = (float*)(ops + pl.off_s1);
+  float* s2 = homo ? s1 : (float*)(ops + pl.off_s2);
+
+  std::vector<PrepJob> jobs;
+  std::vector<PrepItem> pitems;
+  auto mkjob = [&](const float* y, long ld, int n, const float* ref, uint16_t* a, uint16_t* b,
+                   float* sc, float* sig) {
+    PrepJob j{};
+    j.y = y; j.ref = ref; j.outA = a; j.outB = b; j.scale = sc; j.sigma_out = sig;
+    j.wtab = wtab; j.ld = ld; j.m = m; j.n = n; j.kp = pl.kp; j.jchunks = (m + 63) / 64;
+    j.rowlen = pl.rowlen; j.alpha = p.alpha;
+    int id = (int)jobs.size();
+    jobs.push_back(j);
+    for (int t = 0; t < (n + PREP_ROWS - 1) / PREP_ROWS; ++t) pitems.push_back(PrepItem{id, t});
+  };
+  const float* r1 = p.ref_mode == CORR2D_REF_USER ? p.ref1 : nullptr;
+  const float* r2 = p.ref_mode == CORR2D_REF_USER ? (homo ? p.ref1 : p.ref2) : nullptr;
+  if (homo) {
+    mkjob(y1, ld1, n1, r1, opA, opB, s1, sig1);
+  } else {
+    mkjob(y1, ld1, n1, r1, opA, nullptr, s1, sig1);
+    mkjob(y2, ld2, n2, r2, nullptr, opB, s2, sig2);
+  }
+  XProblem xp;
+  memset(&xp, 0, sizeof xp);
+  if ((st = encode_operand(ctx, &xp.tmA, opA, pl.rowlen, n1, TILE_M, pl.planes)) != CORR2D_OK) return st;
+  if ((st = encode_operand(ctx, &xp.tmB, opB, pl.rowlen, n2, tc.bn, pl.planes)) != CORR2D_OK) return st;
+  if ((st = encode_output(ctx, &xp.tmPhi, phi, out_rows, n2, ldo)) != CORR2D_OK) return st;
+  if ((st = encode_output(ctx, &xp.tmPsi, psi, out_rows, n2, ldo)) != CORR2D_OK) return st;
+  xp.s1 = s1;
+  xp.s2 = s2;
+  xp.norm = (float)(p.norm > 0.0 ? p.norm : 1.0 / (kPi * (double)(m - 1)));
+  xp.n1 = n1;
+  xp.n2 = n2;
+  xp.nchunks = pl.nch;
+  xp.mirror = (homo && tc.mirror && tc.bn == TILE_M) ? 1 : 0;
+  xp.bn = tc.bn;
+  xp.out_row_tile0 = out_row_tile0;
+  std::vector<XProblem> probs{xp};
+  std::vector<XItem> xitems;
+  append_tiles(xitems, 0, n1, n2, tc.bn, xp.mirror != 0, ti_begin, ti_end);
+  Blob b = pack(skip_prep ? std::vector<PrepJob>{} : jobs,
+                skip_prep ? std::vector<PrepItem>{} : pitems, probs, xitems);
+  if ((st = upload_blob(ctx, descbuf, desc_last, b)) != CORR2D_OK) return st;
+  uint8_t* d = (uint8_t*)descbuf.p;
+  if (!skip_prep)
+    CUDA_TRY(ctx, launch_prep_tc((const PrepJob*)(d + b.off_jobs),
+                                 (const PrepItem*)(d + b.off_pitems), b.npitems, pl.planes, pl.kp,
+                                 ctx->d_err, ctx->limit_ns, ctx->stream));
+  CUDA_TRY(ctx, launch_xspec_tc((const XProblem*)(d + b.off_probs),
+                                (const XItem*)(d + b.off_xitems), b.nxitems, pl.planes,
+                                ctx->sm_count, ctx->d_err, ctx->limit_ns, ctx->stream));
+  return CORR2D_OK;
+}
+
+corr2d_status enqueue_simt(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1, int n2,
+                           const float* y2, int ld2, const corr2d_params& p, float* phi,
+                           float* psi, long ldo, float* sig1, float* sig2) {
+  const bool homo = (y2 == nullptr);
+  const int kp1 = freq_count(m);
+  const size_t plane1 = align_up((size_t)kp1 * n1 * 4, 256), plane2 = align_up((size_t)kp1 * n2 * 4, 256);
+  const size_t total = 2 * plane1 + 2 * plane2 + align_up((size_t)n1 * 4, 256) + align_up((size_t)n2 * 4, 256);
+  corr2d_status st = ensure(ctx, ctx->ops, total);
+  if (st != CORR2D_OK) return st;
+  const float* tw = nullptr;
+  if ((st = get_simt_twiddles(ctx, m, &tw)) != CORR2D_OK) return st;
+  uint8_t* w = (uint8_t*)ctx->ops.p;
+  float* yr1 = (float*)w; w += plane1;
+  float* yi1 = (float*)w; w += plane1;
+  float* yr2 = (float*)w; w += plane2;
+  float* yi2 = (float*)w; w += plane2;
+  float* s1 = (float*)w; w += align_up((size_t)n1 * 4, 256);
+  float* s2 = homo ? s1 : (float*)w;
+  SimtPrepJob j{};
+  j.y = y1; j.ld = ld1; j.m = m; j.n = n1; j.kp1 = kp1; j.alpha = p.alpha; j.tw = tw;
+  j.ref = p.ref_mode == CORR2D_REF_USER ? p.ref1 : nullptr;
+  j.yr = yr1; j.yi = yi1; j.scale = s1; j.sigma_out = sig1;
+  j.yrw = homo ? yr2 : nullptr; j.yiw = homo ? yi2 : nullptr;
+  CUDA_TRY(ctx, launch_prep_simt(j, ctx->stream));
+  if (!homo) {
+    SimtPrepJob k = j;
+    k.y = y2; k.ld = ld2; k.n = n2; k.ref = p.ref_mode == CORR2D_REF_USER ? p.ref2 : nullptr;
+    // only the weighted planes of stack 2 are read by the cross-spectrum
+    k.yr = nullptr; k.yi = nullptr; k.yrw = yr2; k.yiw = yi2; k.scale = s2; k.sigma_out = sig2;
+    CUDA_TRY(ctx, launch_prep_simt(k, ctx->stream));
+  }
+  const float norm = (float)(p.norm > 0.0 ? p.norm : 1.0 / (kPi * (double)(m - 1)));
+  const bool mirror = homo && !(p.flags & CORR2D_FLAG_NO_MIRROR);
+  CUDA_TRY(ctx, launch_xspec_simt(kp1, n1, homo ? n1 : n2, yr1, yi1, yr2, yi2, s1, s2, norm, phi,
+                                  psi, ldo, mirror, ctx->stream));
+  return CORR2D_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// twiddle table (host): rows c = 0..2K'p-1 of W, c < K'p: cos(2 pi w j / m),
+// c >= K'p: -sin(2 pi w j / m) with w = c - K'p; rows beyond K are zero.
+// Angles use the integer part (w j) mod m.  Stored per 64-step chunk and
+// plane as 128-byte-swizzled rows, the layout tcgen05 reads from shared memory.
+// ---------------------------------------------------------------------------
+size_t c2d::make_twiddles(int m, int planes, uint8_t* out) {
+  const int kp = freq_padded(m, planes);
+  const int K = freq_count(m) - 1;
+  const int ncomp = 2 * kp;
+  const int jchunks = (m + 63) / 64;
+  const size_t block = (size_t)ncomp * 128;
+  const size_t total = block * planes * jchunks;
+  if (!out) return total;
+  memset(out, 0, total);
+  for (int kc = 0; kc < jchunks; ++kc)
+    for (int c = 0; c < ncomp; ++c) {
+      const int w = c < kp ? c : c - kp;
+      if (w > K) continue;
+      for (int jj = 0; jj < 64; ++jj) {
+        const int j = kc * 64 + jj;
+        if (j >= m) break;
+        const long r = ((long)w * (long)j) % (long)m;
+        const double th = 2.0 * kPi * (double)r / (double)m;
+        const double val = c < kp ? std::cos(th) : -std::sin(th);
+        const size_t off = (size_t)c * 128 + ((((size_t)jj / 8) ^ ((size_t)c & 7)) << 4) +
+                           (size_t)(jj % 8) * 2;
+        if (planes == 2) {
+          __half hi = __double2half(val);
+          __half lo = __double2half(val - (double)__half2float(hi));
+          uint16_t h = __half_as_ushort(hi), l = __half_as_ushort(lo);
+          memcpy(out + ((size_t)kc * planes + 0) * block + off, &h, 2);
+          memcpy(out + ((size_t)kc * planes + 1) * block + off, &l, 2);
+        } else {
+          __nv_bfloat16 b = __double2bfloat16(val);
+          uint16_t h = __bfloat16_as_ushort(b);
+          memcpy(out + (size_t)kc * block + off, &h, 2);
+        }
+      }
+    }
+  return total;
+}
+
+// ============================================================================ ABI
+extern "C" {
+
+const char* corr2d_version(void) { return "corr2d-gb300 0.1 (sm_103a)"; }
+
+corr2d_status corr2d_params_default(corr2d_params* p) {
+  if (!p) return CORR2D_EINVAL;
+  memset(p, 0, sizeof *p);
+  p->ref_mode = CORR2D_REF_MEAN;
+  p->norm = 0.0;
+  p->alpha = 0.0;
+  p->precision = CORR2D_PREC_SPLIT;
+  p->flags = 0;
+  return CORR2D_OK;
+}
+
+corr2d_status corr2d_create(corr2d_ctx** out, int device, void* cuda_stream) {
+  if (!out) return fail(nullptr, CORR2D_EINVAL, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(nullptr, CORR2D_ECUDA, "no CUDA device available");
+  }
+  if (device < 0 || device >= ndev) return fail(nullptr, CORR2D_EINVAL, "device %d out of range", device);
+  DeviceGuard g(device);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess)
+    return fail(nullptr, CORR2D_ECUDA, "cannot query device %d", device);
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(nullptr, CORR2D_EUNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a",
+                device, prop.major, prop.minor);
+  std::unique_ptr<corr2d_ctx> ctx(new corr2d_ctx);
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->sm_count = prop.multiProcessorCount;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess || !fn)
+    return fail(nullptr, CORR2D_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  ctx->encode = (PFN_encodeTiled)fn;
+  if (init_prep_kernels() != cudaSuccess || init_xspec_kernels() != cudaSuccess)
+    return fail(nullptr, CORR2D_ECUDA, "kernel attribute setup failed: %s",
+                cudaGetErrorString(cudaGetLastError()));
+  if (cudaMalloc(&ctx->d_err, 256) != cudaSuccess)
+    return fail(nullptr, CORR2D_ENOMEM, "cannot allocate the error word");
+  if (cudaMemset(ctx->d_err, 0, 256) != cudaSuccess)
+    return fail(nullptr, CORR2D_ECUDA, "cannot clear the error word");
+  if (const char* lim = getenv("CORR2D_WAIT_LIMIT_MS")) {
+    long v = atol(lim);
+    if (v > 0) ctx->limit_ns = (unsigned long long)v * 1000000ull;
+  }
+  if (const char* f = getenv("CORR2D_FAULT")) ctx->fault_alloc = (strcmp(f, "alloc") == 0);
+  *out = ctx.release();
+  return CORR2D_OK;
+}
+
+corr2d_status corr2d_destroy(corr2d_ctx* ctx) {
+  if (!ctx) return CORR2D_EINVAL;
+  DeviceGuard g(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  release(ctx->ops);
+  release(ctx->desc);
+  release(ctx->host_in);
+  release(ctx->host_out);
+  release(ctx->batch.desc);
+  release(ctx->batch.ops);
+  if (ctx->batch.exec) cudaGraphExecDestroy(ctx->batch.exec);
+  for (auto& kv : ctx->twiddles) release(kv.second);
+  for (auto& kv : ctx->simt_tw) release(kv.second);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  delete ctx;
+  return CORR2D_OK;
+}
+
+corr2d_status corr2d_set_stream(corr2d_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return CORR2D_EINVAL;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return CORR2D_OK;
+}
+
+const char* corr2d_last_error(const corr2d_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+corr2d_status corr2d_synchronize(corr2d_ctx* ctx) {
+  if (!ctx) return CORR2D_EINVAL;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess)
+    return fail(ctx, CORR2D_ECUDA, "stream synchronize failed: %s", cudaGetErrorString(e));
+  int word = 0;
+  CUDA_TRY(ctx, cudaMemcpy(&word, ctx->d_err, sizeof word, cudaMemcpyDeviceToHost));
+  if (word != DEV_OK) {
+    CUDA_TRY(ctx, cudaMemset(ctx->d_err, 0, sizeof word));
+    if (word == DEV_BAD_AXIS)
+      return fail(ctx, CORR2D_EINVAL, "preprocess: raw axis is not strictly increasing and finite");
+    return fail(ctx, CORR2D_ETIMEOUT, "a device-side wait exceeded its limit; results are invalid");
+  }
+  ctx->err.clear();
+  return CORR2D_OK;
+}
+
+corr2d_status corr2d_preprocess(corr2d_ctx* ctx, int m, int n_raw, const double* x_raw,
+                                const float* y_raw, int n_out, float* y_out, const float* ref,
+                                float* dyn_out) {
+  if (!ctx) return CORR2D_EINVAL;
+  if (m < 1 || n_raw < 2 || n_out < 2)
+    return fail(ctx, CORR2D_EINVAL, "preprocess needs m >= 1, n_raw >= 2, n_out >= 2");
+  if (!x_raw || !y_raw || !y_out) return fail(ctx, CORR2D_EINVAL, "NULL buffer");
+  if ((ref == nullptr) != (dyn_out == nullptr))
+    return fail(ctx, CORR2D_EINVAL, "ref and dyn_out go together");
+  DeviceGuard g(ctx->device);
+  for (const void* q : {(const void*)x_raw, (const void*)y_raw, (const void*)y_out})
+    if (!is_device_ptr(q, ctx->device)) return fail(ctx, CORR2D_EINVAL, "buffers must be device memory");
+  if (ref && (!is_device_ptr(ref, ctx->device) || !is_device_ptr(dyn_out, ctx->device)))
+    return fail(ctx, CORR2D_EINVAL, "buffers must be device memory");
+  CUDA_TRY(ctx, launch_interp(m, n_raw, x_raw, y_raw, n_out, y_out, ref, dyn_out, ctx->d_err,
+                              ctx->stream));
+  ctx->err.clear();
+  return CORR2D_OK;
+}
+
+static corr2d_status validate_compute(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1,
+                                      int n2, const float* y2, int ld2, const corr2d_params& p,
+                                      const float* phi, const float* psi, long ldo,
+                                      bool device_buffers) {
+  const bool homo = (y2 == nullptr);
+  if (m < 2) return fail(ctx, CORR2D_EINVAL, "m = %d: at least 2 perturbation steps are needed (norm divides by m - 1)", m);
+  if (n1 < 1 || !y1) return fail(ctx, CORR2D_EINVAL, "stack 1 is empty or NULL");
+  if (ld1 < n1) return fail(ctx, CORR2D_EINVAL, "ld1 < n1");
+  if (!homo && (n2 < 1 || ld2 < n2)) return fail(ctx, CORR2D_EINVAL, "bad stack 2 shape");
+  const int n2e = homo ? n1 : n2;
+  if (!phi || !psi) return fail(ctx, CORR2D_EINVAL, "phi/psi are NULL");
+  if (ldo < n2e) return fail(ctx, CORR2D_EINVAL, "ldo < n2");
+  corr2d_status st = check_params(ctx, &p, homo);
+  if (st != CORR2D_OK) return st;
+  const bool tc = p.precision != CORR2D_PREC_FP32;
+  if (!tc && m > MAX_M_FP32)
+    return fail(ctx, CORR2D_EUNSUPPORTED, "the FP32 path supports m <= %d", MAX_M_FP32);
+  if (tc) {
+    if (m > MAX_M_TC)
+      return fail(ctx, CORR2D_EUNSUPPORTED, "tensor-core precisions support m <= %d (use FP32)", MAX_M_TC);
+    if (device_buffers && (ldo % 4 != 0 || ((uintptr_t)phi & 15) || ((uintptr_t)psi & 15)))
+      return fail(ctx, CORR2D_EINVAL, "TMA stores need ldo %% 4 == 0 and 16-byte aligned phi/psi");
+    if ((long)(n1 + TILE_M - 1) / TILE_M > 65535 || (long)(n2e + 63) / 64 > 65535)
+      return fail(ctx, CORR2D_EUNSUPPORTED, "n too large for the tile index");
+  }
+  if (device_buffers) {
+    const void* ptrs[4] = {y1, y2, phi, psi};
+    for (const void* q : ptrs)
+      if (q && !is_device_ptr(q, ctx->device))
+        return fail(ctx, CORR2D_EINVAL, "stack and output buffers must be device memory of device %d", ctx->device);
+  }
+  return CORR2D_OK;
+}
+
+// Tuned tile choice for a shape; tries the candidates once (timed with events)
+// on the caller's buffers and caches the fastest.
+static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1,
+                                  int n2, const float* y2, int ld2, const corr2d_params& p,
+                                  float* phi, float* psi, long ldo, TileChoice* out) {
+  const bool homo = (y2 == nullptr);
+  const int n2e = homo ? n1 : n2;
+  auto key = std::make_tuple(m, n1, n2e, homo ? 1 : 0, p.precision * 2 + ((p.flags & CORR2D_FLAG_NO_MIRROR) ? 1 : 0));
+  auto it = ctx->tuned.find(key);
+  if (it != ctx->tuned.end()) { *out = it->second; return CORR2D_OK; }
+  std::vector<TileChoice> cands;
+  if (homo && !(p.flags & CORR2D_FLAG_NO_MIRROR)) cands.push_back(TileChoice{128, 1});
+  cands.push_back(TileChoice{128, 0});
+  cands.push_back(TileChoice{64, 0});
+  if (getenv("CORR2D_NO_TUNE") || cands.size() == 1) {
+    *out = cands[0];
+    ctx->tuned[key] = *out;
+    return CORR2D_OK;
+  }
+  cudaEvent_t e0, e1;
+  CUDA_TRY(ctx, cudaEventCreate(&e0));
+  CUDA_TRY(ctx, cudaEventCreate(&e1));
+  float best = 1e30f;
+  TileChoice bestc = cands[0];
+  const int ti_end = (n1 + TILE_M - 1) / TILE_M;
+  for (const TileChoice& c : cands) {
+    float tsum = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {  // first run warms up, second is timed
+      cudaEventRecord(e0, ctx->stream);
+      corr2d_status st = enqueue_tc(ctx, m, n1, y1, ld1, n2e, y2, ld2, p, phi, psi, ldo, n1, nullptr,
+                                    nullptr, c, 0, ti_end, 0, false, ctx->ops, ctx->desc,
+                                    ctx->desc_host);
+      if (st != CORR2D_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+      cudaEventRecord(e1, ctx->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep == 1) tsum = ms;
+    }
+    if (tsum < best) { best = tsum; bestc = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->tuned[key] = bestc;
+  *out = bestc;
+  return CORR2D_OK;
+}
+
+corr2d_status corr2d_compute(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1, int n2,
+                             const float* y2, int ld2, const corr2d_params* params, float* phi,
+                             float* psi, long ldo, float* sigma1_out, float* sigma2_out) {
+  if (!ctx) return CORR2D_EINVAL;
+  corr2d_params p;
+  if (params) p = *params; else corr2d_params_default(&p);
+  DeviceGuard g(ctx->device);
+  corr2d_status st = validate_compute(ctx, m, n1, y1, ld1, n2, y2, ld2, p, phi, psi, ldo, true);
+  if (st != CORR2D_OK) return st;
+  const bool homo = (y2 == nullptr);
+  if (homo) { n2 = n1; ld2 = ld1; }
+  if ((sigma1_out && !is_device_ptr(sigma1_out, ctx->device)) ||
+      (sigma2_out && !is_device_ptr(sigma2_out, ctx->device)))
+    return fail(ctx, CORR2D_EINVAL, "sigma outputs must be device memory");
+  if (p.precision == CORR2D_PREC_FP32) {
+    st = enqueue_simt(ctx, m, n1, y1, ld1, n2, homo ? nullptr : y2, ld2, p, phi, psi, ldo,
+                      sigma1_out, homo ? nullptr : sigma2_out);
+  } else {
+    TileChoice tc;
+    st = choose_tiles(ctx, m, n1, y1, ld1, n2, homo ? nullptr : y2, ld2, p, phi, psi, ldo, &tc);
+    if (st != CORR2D_OK) return st;
+    st = enqueue_tc(ctx, m, n1, y1, ld1, n2, homo ? nullptr : y2, ld2, p, phi, psi, ldo, n1,
+                    sigma1_out, homo ? nullptr : sigma2_out, tc, 0, (n1 + TILE_M - 1) / TILE_M, 0,
+                    false, ctx->ops, ctx->desc, ctx->desc_host);
+  }
+  if (st != CORR2D_OK) return st;
+  if (homo && sigma2_out && sigma1_out)
+    CUDA_TRY(ctx, cudaMemcpyAsync(sigma2_out, sigma1_out, (size_t)n1 * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  else if (homo && sigma2_out)
+    return fail(ctx, CORR2D_EINVAL, "homo correlation: pass sigma1_out to get sigma2_out");
+  ctx->err.clear();
+  return CORR2D_OK;
+}
+
+corr2d_status corr2d_compute_host(corr2d_ctx* ctx, int m, int n1, const float* y1, int n2,
+                                  const float* y2, const corr2d_params* params, float* phi,
+                                  float* psi, long ldo) {
+  if (!ctx) return CORR2D_EINVAL;
+  corr2d_params p;
+  if (params) p = *params; else corr2d_params_default(&p);
+  DeviceGuard g(ctx->device);
+  corr2d_status st = validate_compute(ctx, m, n1, y1, n1, n2, y2, n2, p, phi, psi, ldo, false);
+  if (st != CORR2D_OK) return st;
+  if (p.precision == CORR2D_PREC_FP32)
+    return fail(ctx, CORR2D_EUNSUPPORTED, "the host-buffer path runs the tensor-core precisions");
+  if (p.ref_mode == CORR2D_REF_USER)
+    return fail(ctx, CORR2D_EUNSUPPORTED, "the host-buffer path uses the perturbation-mean reference");
+  const bool homo = (y2 == nullptr);
+  if (homo) n2 = n1;
+  // stacks to the device
+  const size_t b1 = align_up((size_t)m * n1 * 4, 256), b2 = homo ? 0 : align_up((size_t)m * n2 * 4, 256);
+  if ((st = ensure(ctx, ctx->host_in, b1 + b2)) != CORR2D_OK) return st;
+  float* d1 = (float*)ctx->host_in.p;
+  float* d2 = homo ? nullptr : (float*)((uint8_t*)ctx->host_in.p + b1);
+  CUDA_TRY(ctx, cudaMemcpyAsync(d1, y1, (size_t)m * n1 * 4, cudaMemcpyHostToDevice, ctx->stream));
+  if (!homo) CUDA_TRY(ctx, cudaMemcpyAsync(d2, y2, (size_t)m * n2 * 4, cudaMemcpyHostToDevice, ctx->stream));
+  // output slabs: rows of 128-row tiles, two slab buffers so copies overlap kernels
+  const int nt1 = (n1 + TILE_M - 1) / TILE_M;
+  const long ld_dev = align_up((size_t)n2, 4);
+  int slab_tiles = (int)std::max<long>(1, std::min<long>(nt1, (256l << 20) / ((long)TILE_M * ld_dev * 8)));
+  const size_t slab_bytes = align_up((size_t)slab_tiles * TILE_M * ld_dev * 4, 1024);
+  if ((st = ensure(ctx, ctx->host_out, 4 * slab_bytes)) != CORR2D_OK) return st;
+  cudaStream_t copy;
+  CUDA_TRY(ctx, cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking));
+  cudaEvent_t done[2], freed[2];
+  for (int i = 0; i < 2; ++i) {
+    cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&freed[i], cudaEventDisableTiming);
+  }
+  TileChoice tc{128, 0};
+  corr2d_status result = CORR2D_OK;
+  std::vector<uint8_t> last;  // slab descriptors differ per slab
+  DevBuf slab_desc[2];
+  std::vector<uint8_t> slab_last[2];
+  int k = 0;
+  for (int t0 = 0; t0 < nt1; t0 += slab_tiles, ++k) {
+    const int t1 = std::min(nt1, t0 + slab_tiles);
+    const int sb = k & 1;
+    float* sphi = (float*)((uint8_t*)ctx->host_out.p + (2 * sb) * slab_bytes);
+    float* spsi = (float*)((uint8_t*)ctx->host_out.p + (2 * sb + 1) * slab_bytes);
+    if (k >= 2) cudaStreamWaitEvent(ctx->stream, freed[sb], 0);
+    const int rows = std::min(n1, t1 * TILE_M) - t0 * TILE_M;
+    result = enqueue_tc(ctx, m, n1, d1, n1, n2, d2, n2, p, sphi, spsi, ld_dev, rows, nullptr,
+                        nullptr, tc, t0, t1, t0, k > 0, ctx->ops, slab_desc[sb], slab_last[sb]);
+    if (result != CORR2D_OK) break;
+    cudaEventRecord(done[sb], ctx->stream);
+    cudaStreamWaitEvent(copy, done[sb], 0);
+    cudaError_t e1 = cudaMemcpy2DAsync(phi + (size_t)t0 * TILE_M * ldo, ldo * 4, sphi, ld_dev * 4,
+                                       (size_t)n2 * 4, rows, cudaMemcpyDeviceToHost, copy);
+    cudaError_t e2 = cudaMemcpy2DAsync(psi + (size_t)t0 * TILE_M * ldo, ldo * 4, spsi, ld_dev * 4,
+                                       (size_t)n2 * 4, rows, cudaMemcpyDeviceToHost, copy);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      result = fail(ctx, CORR2D_ECUDA, "device-to-host copy failed: %s",
+                    cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+      break;
+    }
+    cudaEventRecord(freed[sb], copy);
+  }
+  cudaStreamSynchronize(copy);
+  cudaStreamSynchronize(ctx->stream);
+  for (int i = 0; i < 2; ++i) {
+    cudaEventDestroy(done[i]);
+    cudaEventDestroy(freed[i]);
+    release(slab_desc[i]);
+  }
+  cudaStreamDestroy(copy);
+  (void)last;
+  if (result != CORR2D_OK) return result;
+  return corr2d_synchronize(ctx);
+}
+
+// ---------------------------------------------------------------------------- batch
+corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
+                           const corr2d_params* shared_params) {
+  if (!ctx) return CORR2D_EINVAL;
+  corr2d_params p;
+  if (shared_params) p = *shared_params; else corr2d_params_default(&p);
+  if (count < 0 || (count > 0 && !hp)) return fail(ctx, CORR2D_EINVAL, "bad problem list");
+  if (count == 0) return CORR2D_OK;
+  if (p.ref_mode != CORR2D_REF_MEAN)
+    return fail(ctx, CORR2D_EINVAL, "batch: only the perturbation-mean reference is supported");
+  if (p.precision == CORR2D_PREC_FP32)
+    return fail(ctx, CORR2D_EUNSUPPORTED, "batch runs the tensor-core precisions");
+  DeviceGuard g(ctx->device);
+  for (int i = 0; i < count; ++i) {
+    const corr2d_problem& q = hp[i];
+    corr2d_status st = validate_compute(ctx, q.m, q.n1, q.y1, q.n1, q.n2, q.y2, q.n2, p, q.phi,
+                                        q.psi, q.ldo, true);
+    if (st != CORR2D_OK) return fail(ctx, st, "problem %d: %s", i, ctx->err.c_str());
+  }
+  // key: the problem list and the parameters
+  std::vector<uint8_t> key(sizeof(corr2d_problem) * count + sizeof(corr2d_params));
+  memcpy(key.data(), hp, sizeof(corr2d_problem) * count);
+  memcpy(key.data() + sizeof(corr2d_problem) * count, &p, sizeof p);
+  BatchCache& bc = ctx->batch;
+  if (bc.exec && bc.key == key) {
+    CUDA_TRY(ctx, cudaGraphLaunch(bc.exec, ctx->stream));
+    ctx->err.clear();
+    return CORR2D_OK;
+  }
+  const int planes = p.precision == CORR2D_PREC_SPLIT ? 2 : 1;
+  // workspace layout
+  std::vector<size_t> offA(count), offB(count), offS1(count), offS2(count);
+  size_t total = 0;
+  int max_kp = 0;
+  for (int i = 0; i < count; ++i) {
+    const corr2d_problem& q = hp[i];
+    const bool homo = q.y2 == nullptr;
+    const int n2 = homo ? q.n1 : q.n2;
+    TcPlan pl = plan_tc(q.m, q.n1, n2, homo, p.precision);
+    max_kp = std::max(max_kp, pl.kp);
+    offA[i] = total; total += pl.bytesA;
+    offB[i] = total; total += pl.bytesB;
+    offS1[i] = total; total += align_up((size_t)q.n1 * 4, 256);
+    offS2[i] = total; total += align_up((size_t)n2 * 4, 256);
+  }
+  corr2d_status st = ensure(ctx, bc.ops, total);
+  if (st != CORR2D_OK) return st;
+  uint8_t* ops = (uint8_t*)bc.ops.p;
+  // tuned tile width per problem: bn = 64 for problems whose 128-wide tile
+  // count would leave SMs idle, chosen by timing thresholds below
+  auto build = [&](int bn_threshold, std::vector<PrepJob>& jobs, std::vector<PrepItem>& pitems,
+                   std::vector<XProblem>& probs, std::vector<XItem>& xitems) -> corr2d_status {
+    jobs.clear(); pitems.clear(); probs.clear(); xitems.clear();
+    for (int i = 0; i < count; ++i) {
+      const corr2d_problem& q = hp[i];
+      const bool homo = q.y2 == nullptr;
+      const int n2 = homo ? q.n1 : q.n2;
+      TcPlan pl = plan_tc(q.m, q.n1, n2, homo, p.precision);
+      const uint8_t* wtab = nullptr;
+      corr2d_status s2 = get_twiddles(ctx, q.m, planes, &wtab);
+      if (s2 != CORR2D_OK) return s2;
+      uint16_t* opA = (uint16_t*)(ops + offA[i]);
+      uint16_t* opB = (uint16_t*)(ops + offB[i]);
+      float* sc1 = (float*)(ops + offS1[i]);
+      float* sc2 = homo ? sc1 : (float*)(ops + offS2[i]);
+      auto mkjob = [&](const float* y, int n, uint16_t* a, uint16_t* b, float* sc) {
+        PrepJob j{};
+        j.y = y; j.ref = nullptr; j.outA = a; j.outB = b; j.scale = sc; j.sigma_out = nullptr;
+        j.wtab = wtab; j.ld = n; j.m = q.m; j.n = n; j.kp = pl.kp; j.jchunks = (q.m + 63) / 64;
+        j.rowlen = pl.rowlen; j.alpha = p.alpha;
+        int id = (int)jobs.size();
+        jobs.push_back(j);
+        for (int t = 0; t < (n + PREP_ROWS - 1) / PREP_ROWS; ++t) pitems.push_back(PrepItem{id, t});
+      };
+      if (homo) {
+        mkjob(q.y1, q.n1, opA, opB, sc1);
+      } else {
+        mkjob(q.y1, q.n1, opA, nullptr, sc1);
+        mkjob(q.y2, n2, nullptr, opB, sc2);
+      }
+      const int bn = (std::max(q.n1, n2) <= bn_threshold) ? 64 : 128;
+      XProblem xp;
+      memset(&xp, 0, sizeof xp);
+      if ((s2 = encode_operand(ctx, &xp.tmA, opA, pl.rowlen, q.n1, TILE_M, planes)) != CORR2D_OK) return s2;
+      if ((s2 = encode_operand(ctx, &xp.tmB, opB, pl.rowlen, n2, bn, planes)) != CORR2D_OK) return s2;
+      if ((s2 = encode_output(ctx, &xp.tmPhi, q.phi, q.n1, n2, q.ldo)) != CORR2D_OK) return s2;
+      if ((s2 = encode_output(ctx, &xp.tmPsi, q.psi, q.n1, n2, q.ldo)) != CORR2D_OK) return s2;
+      xp.s1 = sc1; xp.s2 = sc2;
+      xp.norm = (float)(p.norm > 0.0 ? p.norm : 1.0 / (kPi * (double)(q.m - 1)));
+      xp.n1 = q.n1; xp.n2 = n2; xp.nchunks = pl.nch;
+      xp.mirror = (homo && bn == 128 && !(p.flags & CORR2D_FLAG_NO_MIRROR)) ? 1 : 0;
+      xp.bn = bn;
+      xp.out_row_tile0 = 0;
+      probs.push_back(xp);
+    }
+    // tiles, longest first (more chunks = more MMA work), stable within a problem
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return probs[a].nchunks > probs[b].nchunks;
+    });
+    for (int i : order)
+      append_tiles(xitems, i, probs[i].n1, probs[i].n2, probs[i].bn, probs[i].mirror != 0, 0,
+                   (probs[i].n1 + TILE_M - 1) / TILE_M);
+    return CORR2D_OK;
+  };
+  auto make_graph = [&](int bn_threshold, cudaGraphExec_t* exec) -> corr2d_status {
+    std::vector<PrepJob> jobs;
+    std::vector<PrepItem> pitems;
+    std::vector<XProblem> probs;
+    std::vector<XItem> xitems;
+    corr2d_status s2 = build(bn_threshold, jobs, pitems, probs, xitems);
+    if (s2 != CORR2D_OK) return s2;
+    Blob b = pack(jobs, pitems, probs, xitems);
+    std::vector<uint8_t> last;
+    if ((s2 = ensure(ctx, bc.desc, b.bytes.size())) != CORR2D_OK) return s2;
+    CUDA_TRY(ctx, cudaMemcpyAsync(bc.desc.p, b.bytes.data(), b.bytes.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    uint8_t* d = (uint8_t*)bc.desc.p;
+    cudaStream_t cs;
+    CUDA_TRY(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph;
+    CUDA_TRY(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = launch_prep_tc((const PrepJob*)(d + b.off_jobs), (const PrepItem*)(d + b.off_pitems),
+                                    b.npitems, planes, max_kp, ctx->d_err, ctx->limit_ns, cs);
+    cudaError_t e2 = launch_xspec_tc((const XProblem*)(d + b.off_probs), (const XItem*)(d + b.off_xitems),
+                                     b.nxitems, planes, ctx->sm_count, ctx->d_err, ctx->limit_ns, cs);
+    cudaError_t e3 = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+      return fail(ctx, CORR2D_ECUDA, "batch graph capture failed: %s / %s / %s", cudaGetErrorString(e1),
+                  cudaGetErrorString(e2), cudaGetErrorString(e3));
+    cudaError_t e4 = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e4 != cudaSuccess) return fail(ctx, CORR2D_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e4));
+    return CORR2D_OK;
+  };
+  if (bc.exec) { cudaGraphExecDestroy(bc.exec); bc.exec = nullptr; }
+  // tuner: time the batch graph for each tile-width threshold, keep the fastest
+  const int thresholds[] = {0, 1024, 2048};
+  int best_thr = 0;
+  if (!getenv("CORR2D_NO_TUNE")) {
+    cudaEvent_t e0, e1;
+    CUDA_TRY(ctx, cudaEventCreate(&e0));
+    CUDA_TRY(ctx, cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int thr : thresholds) {
+      cudaGraphExec_t ex = nullptr;
+      if ((st = make_graph(thr, &ex)) != CORR2D_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, ctx->stream);
+        cudaGraphLaunch(ex, ctx->stream);
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+      }
+      cudaGraphExecDestroy(ex);
+      if (ms < best) { best = ms; best_thr = thr; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  if ((st = make_graph(best_thr, &bc.exec)) != CORR2D_OK) return st;
+  bc.key = key;
+  CUDA_TRY(ctx, cudaGraphLaunch(bc.exec, ctx->stream));
+  ctx->err.clear();
+  return CORR2D_OK;
+}
+
+}  // extern "C"

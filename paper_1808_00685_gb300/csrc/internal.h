@@ -1,0 +1,134 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace c2d {
+
+// ----------------------------------------------------------------------------
+// Operand layout of the tensor-core path.
+//
+// Each spectral variable nu gets one operand row of `rowlen` 16-bit elements
+// holding its half spectrum Y(nu, omega), omega = 0..K'p-1 (K'p = K+1 rounded
+// up to a multiple of g), scaled by a power of two 2^E(nu) that puts the row
+// maximum in [2^13, 2^14).  The row is a sequence of 128-byte chunks, each
+// covering g frequencies:
+//   SPLIT (FP16 hi/lo, g = 16): [Re_hi(16) Im_hi(16) Re_lo(16) Im_lo(16)]
+//   BF16  (g = 32):             [Re(32) Im(32)]
+// with hi = fp16(v), lo = fp16(v - hi).  The "B" operand of stack 2 carries
+// the half-spectrum weight w (1 for omega = 0, else 2); the "A" operand of
+// stack 1 does not.  A chunk is exactly one 128-byte swizzle row, so one TMA
+// box of 64 elements x rows lands in shared memory ready for tcgen05.mma.
+// ----------------------------------------------------------------------------
+constexpr int CHUNK_ELEMS = 64;   // 16-bit elements per 128-byte chunk
+constexpr int TILE_M = 128;       // nu1 rows per MMA tile (TMEM lanes)
+constexpr int TILE_N = 128;       // nu2 columns per tile (Phi and Psi each)
+constexpr int PREP_ROWS = 128;    // spectral variables per DFT tile
+constexpr int MAX_M_TC = 512;     // largest m accepted by the tensor-core path
+constexpr int kMaxDynSmem = 232448;  // dynamic shared memory per CTA (227 KB)
+constexpr int MAX_M_FP32 = 1600;     // FP32 DFT keeps m x 32 centred values in smem
+
+inline int freq_count(int m) { return (m - 1) / 2 + 1; }          // K + 1
+inline int freq_group(int planes) { return planes == 2 ? 16 : 32; }
+inline int freq_padded(int m, int planes) {
+  int g = freq_group(planes);
+  return (freq_count(m) + g - 1) / g * g;
+}
+inline int chunks_for(int m, int planes) { return freq_padded(m, planes) / freq_group(planes); }
+
+// One stack's DFT job (tensor-core prep kernel).
+struct PrepJob {
+  const float* y;          // m x n, leading dimension ld
+  const float* ref;        // user reference (nullable -> perturbation mean)
+  uint16_t* outA;          // unweighted operand rows (nullable)
+  uint16_t* outB;          // weighted operand rows (nullable)
+  float* scale;            // n: sigma^-alpha * 2^-E(nu)
+  float* sigma_out;        // n (nullable)
+  const uint8_t* wtab;     // pre-swizzled twiddles of this m (see make_twiddles)
+  long ld;
+  int m, n;
+  int kp;                  // K'p
+  int jchunks;             // ceil(m / 64)
+  int rowlen;              // operand row length in elements
+  int pad_;
+  double alpha;
+};
+
+// One work item of the prep kernel: (job, 128-variable tile).
+struct PrepItem {
+  int job;
+  int tile;
+};
+
+// One correlation problem of the cross-spectrum kernel.  Tensor maps first:
+// they must be 64-byte aligned.
+struct alignas(128) XProblem {
+  CUtensorMap tmA;     // operand rows of stack 1: {rowlen, n1}, box {64, 128}
+  CUtensorMap tmB;     // operand rows of stack 2 (weighted): {rowlen, n2}, box {64, bn}
+  CUtensorMap tmPhi;   // output {n2, n1}, box {32, 32}, 128-byte swizzle
+  CUtensorMap tmPsi;
+  const float* s1;     // scale vectors (stack 1 / stack 2)
+  const float* s2;
+  float norm;
+  int n1, n2;
+  int nchunks;         // operand chunks per row
+  int mirror;          // 1: homo tile with its mirror written too (bn == 128)
+  int bn;              // nu2 columns per tile: 64 or 128
+  int out_row_tile0;   // output rows are shifted up by out_row_tile0 * 128
+  int pad_[3];
+};
+
+// One tile of the cross-spectrum kernel: problem index and tile coordinates.
+struct XItem {
+  int prob;
+  uint16_t ti, tj;
+};
+
+// Host side: build the pre-swizzled twiddle table for m (FP64 angles with
+// the integer part reduced modulo m, split into 16-bit planes).  Returns the
+// table size in bytes; writes it into `out` when non-null.
+size_t make_twiddles(int m, int planes, uint8_t* out);
+
+// One-time kernel attribute setup (dynamic shared memory limits); called when
+// a context is created, so that later launches may be captured in graphs.
+cudaError_t init_prep_kernels();
+cudaError_t init_xspec_kernels();
+
+// Launchers (return cudaGetLastError()).
+cudaError_t launch_prep_tc(const PrepJob* d_jobs, const PrepItem* d_items, int nitems, int planes,
+                           int max_kp, int* err, unsigned long long limit_ns, cudaStream_t s);
+cudaError_t launch_xspec_tc(const XProblem* d_probs, const XItem* d_items, int nitems,
+                            int planes, int grid, int* err, unsigned long long limit_ns,
+                            cudaStream_t s);
+
+// FP32 CUDA-core path.
+struct SimtPrepJob {
+  const float* y;
+  const float* ref;
+  float* yr;      // kp1 x n, frequency-major (A: unweighted; nullable)
+  float* yi;
+  float* yrw;     // weighted copies (nullable when not needed)
+  float* yiw;
+  float* scale;   // n: sigma^-alpha
+  float* sigma_out;
+  const float* tw;  // 2*m: cos(2 pi r/m), sin(2 pi r/m)
+  long ld;
+  int m, n, kp1;
+  double alpha;
+};
+cudaError_t launch_prep_simt(const SimtPrepJob& job, cudaStream_t s);
+cudaError_t launch_xspec_simt(int kp1, int n1, int n2, const float* yr1, const float* yi1,
+                              const float* yr2w, const float* yi2w, const float* s1,
+                              const float* s2, float norm, float* phi, float* psi, long ldo,
+                              bool mirror, cudaStream_t s);
+
+// Preprocessing.
+cudaError_t launch_interp(int m, int n_raw, const double* x, const float* y, int n_out,
+                          float* out, const float* ref, float* dyn, int* err, cudaStream_t s);
+
+// Codes of the device error word: a bounded wait ran out, or the
+// preprocessing axis check failed.
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD_AXIS = 2 };
+
+}  // namespace c2d

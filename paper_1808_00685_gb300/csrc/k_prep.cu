@@ -1,0 +1,440 @@
+// Reference spectrum, dynamic spectra, standard deviation and the truncated
+// DFT along the perturbation axis (Eqs. ref, dynspec, stdev, disFT; the half
+// spectrum of Sec. 4.2), producing the operand rows of the cross-spectrum.
+//
+// Tensor-core kernel (k_prep_tc): one CTA per 128 spectral variables, one
+// thread per variable.
+//   1. FP64 reference (perturbation mean or the caller's spectrum), FP64
+//      centering y - ref, FP64 sum of squares and maximum |y - ref|.
+//   2. The centred values, scaled by a power of two, are split into 16-bit
+//      planes (FP16 hi/lo, or one BF16 plane) and written to shared memory as
+//      the A operand (variables x perturbation steps, K-major, 128-byte
+//      swizzle), 64 steps at a time.
+//   3. tcgen05.mma contracts them with the twiddle matrix W (rows: cos and
+//      -sin of 2 pi ((omega j) mod m) / m, FP64-built, split likewise) into
+//      TMEM: D(nu, c) = sum_j y~(nu, j) W(c, j); with planes hi*hi + hi*lo +
+//      lo*hi.  The twiddle chunks arrive by bulk copy.
+//   4. Epilogue: each thread reads its row of D, rescales by a power of two,
+//      splits into planes and writes the operand rows (unweighted for stack 1,
+//      weight w = 1 / 2 for stack 2), the scale factor sigma^-alpha 2^-E and sigma.
+#include <cmath>
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace c2d {
+
+// 16 consecutive TMEM columns of this warp's lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+__device__ __forceinline__ uint32_t pack_b2(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// Split 8 FP64 values into FP16 hi and lo 16-byte vectors.
+__device__ __forceinline__ void split8_f64(const double (&v)[8], uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    __half h0 = __double2half(v[2 * e]), h1 = __double2half(v[2 * e + 1]);
+    __half l0 = __double2half(v[2 * e] - (double)__half2float(h0));
+    __half l1 = __double2half(v[2 * e + 1] - (double)__half2float(h1));
+    h[e] = pack_h2(h0, h1);
+    l[e] = pack_h2(l0, l1);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ uint4 bf16x8_f64(const double (&v)[8]) {
+  uint32_t h[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+    h[e] = pack_b2(__double2bfloat16(v[2 * e]), __double2bfloat16(v[2 * e + 1]));
+  return make_uint4(h[0], h[1], h[2], h[3]);
+}
+
+// FP32 -> FP16 hi/lo of 8 values (with per-value weight multiplier).
+__device__ __forceinline__ void split8_f32(const float* v, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    __half h0 = __float2half_rn(v[2 * e]), h1 = __float2half_rn(v[2 * e + 1]);
+    __half l0 = __float2half_rn(v[2 * e] - __half2float(h0));
+    __half l1 = __float2half_rn(v[2 * e + 1] - __half2float(h1));
+    h[e] = pack_h2(h0, h1);
+    l[e] = pack_h2(l0, l1);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ uint4 bf16x8_f32(const float* v) {
+  uint32_t h[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+    h[e] = pack_b2(__float2bfloat16_rn(v[2 * e]), __float2bfloat16_rn(v[2 * e + 1]));
+  return make_uint4(h[0], h[1], h[2], h[3]);
+}
+
+__device__ __forceinline__ uint32_t tmem_cols_for(int ncomp) {
+  uint32_t c = 32;
+  while ((int)c < ncomp) c <<= 1;
+  return c;
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_prep_tc(const PrepJob* __restrict__ jobs,
+                                                 const PrepItem* __restrict__ items, int* err,
+                                                 unsigned long long limit_ns) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const PrepItem item = items[blockIdx.x];
+  const PrepJob& job = jobs[item.job];
+  const int m = job.m, n = job.n, kp = job.kp;
+  const int ncomp = 2 * kp;  // rows of W: cos block then -sin block
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int nu = item.tile * PREP_ROWS + t;
+  const bool valid = nu < n;
+  const WaitCtl wc{err, limit_ns};
+
+  // shared memory: A planes (128 rows x 128 B each), W planes (ncomp rows x 128 B each)
+  uint8_t* sA = base;
+  uint8_t* sW = base + P * PREP_ROWS * 128;
+  const uint32_t wbytes = (uint32_t)ncomp * 128u;
+  uint64_t* bars = (uint64_t*)(sW + P * wbytes);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2);
+  const uint32_t wbar = smem_u32(&bars[0]), mbar = smem_u32(&bars[1]);
+  const uint32_t ncols = tmem_cols_for(ncomp);
+
+  if (t == 0) {
+    mbar_init(wbar, 1);
+    mbar_init(mbar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(smem_u32(tmem_slot), ncols);
+    tmem_relinquish();
+  }
+  // ---- 1. FP64 reference, sums of squares and range (Eqs. ref, dynspec, stdev)
+  const float* y = job.y;
+  const long ld = job.ld;
+  double ref = 0.0;
+  if (valid) {
+    if (job.ref) {
+      ref = (double)job.ref[nu];
+    } else {
+      double s = 0.0;
+      for (int j = 0; j < m; ++j) s += (double)y[(long)j * ld + nu];
+      ref = s / (double)m;
+    }
+  }
+  double ss = 0.0, amax = 0.0;
+  if (valid) {
+    for (int j = 0; j < m; ++j) {
+      double d = (double)y[(long)j * ld + nu] - ref;
+      ss += d * d;
+      amax = fmax(amax, fabs(d));
+    }
+  }
+  int ey = 0;
+  if (amax > 0.0) {
+    int e;
+    frexp(amax, &e);  // amax < 2^e
+    ey = 14 - e;      // scaled maximum in [2^13, 2^14)
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  // ---- 2./3. A chunks of 64 perturbation steps, MMA with the twiddle chunk
+  const int jchunks = job.jchunks;
+  const int nhalf = ncomp > 256 ? 2 : 1;
+  const int nfirst = ncomp > 256 ? 256 : ncomp;
+  const uint32_t id0 = idesc_f16(128, nfirst, P == 1, false);
+  const uint32_t id1 = idesc_f16(128, ncomp - 256 > 0 ? ncomp - 256 : 16, P == 1, false);
+  int w_armed = 0, m_committed = 0;  // thread 0: async operations started
+  for (int kc = 0; kc < jchunks; ++kc) {
+    if (kc > 0) ok = ok && mbar_wait(mbar, (kc - 1) & 1, wc);  // smem free again
+    if (t == 0 && ok) {
+      mbar_arrive_expect_tx(wbar, P * wbytes);
+      ++w_armed;
+      for (int p = 0; p < P; ++p)
+        bulk_load(smem_u32(sW + p * wbytes), job.wtab + ((size_t)kc * P + p) * wbytes, wbytes,
+                  wbar);
+    }
+    // centred, scaled values of steps 64 kc .. 64 kc + 63 for this variable
+#pragma unroll 1
+    for (int jg = 0; jg < 8; ++jg) {
+      double v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        int j = kc * 64 + jg * 8 + e;
+        v[e] = (valid && j < m) ? ldexp((double)y[(long)j * ld + nu] - ref, ey) : 0.0;
+      }
+      uint32_t off = sw128_off((uint32_t)t, (uint32_t)jg);
+      if (P == 2) {
+        uint4 hi, lo;
+        split8_f64(v, hi, lo);
+        *(uint4*)(sA + off) = hi;
+        *(uint4*)(sA + PREP_ROWS * 128 + off) = lo;
+      } else {
+        *(uint4*)(sA + off) = bf16x8_f64(v);
+      }
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0 && ok) {
+      ok = mbar_wait(wbar, kc & 1, wc);
+      if (ok) {
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA), w0 = smem_u32(sW);
+        const int ncombo = P == 2 ? 3 : 1;
+#pragma unroll 1
+        for (int ks = 0; ks < 4; ++ks) {
+#pragma unroll 1
+          for (int cb = 0; cb < ncombo; ++cb) {
+            // (A plane, W plane): hi*hi, hi*lo, lo*hi
+            const int pa = (cb == 2) ? 1 : 0, pw = (cb == 1) ? 1 : 0;
+            const uint64_t ad = sw128_desc(a0 + pa * PREP_ROWS * 128 + ks * 32);
+            const uint32_t acc = (kc > 0 || ks > 0 || cb > 0) ? 1u : 0u;
+            for (int h = 0; h < nhalf; ++h) {
+              const uint64_t bd = sw128_desc(w0 + pw * wbytes + h * 256 * 128 + ks * 32);
+              mma_f16(tmem + h * 256, ad, bd, h ? id1 : id0, acc);
+            }
+          }
+        }
+        mma_commit(mbar);
+        ++m_committed;
+      }
+    }
+  }
+  ok = ok && mbar_wait(mbar, (jchunks - 1) & 1, wc);
+  tc_fence_after();
+
+  // ---- 4. epilogue: row maximum, power-of-two rescale, planes, operand rows
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  float dmax = 0.f;
+  for (int c0 = 0; c0 < ncomp; c0 += 16) {
+    float v[16];
+    tmem_ld16(trow + c0, v);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) dmax = fmaxf(dmax, fabsf(v[i]));
+  }
+  int eY = 0;
+  if (dmax > 0.f) {
+    int e;
+    frexpf(dmax, &e);
+    eY = 14 - e;
+  }
+  const float fY = ldexpf(1.0f, eY);
+  const int g = (P == 2) ? 16 : 32;
+  const int nch = kp / g;
+  uint8_t* rowA = job.outA ? (uint8_t*)(job.outA + (size_t)(valid ? nu : 0) * job.rowlen) : nullptr;
+  uint8_t* rowB = job.outB ? (uint8_t*)(job.outB + (size_t)(valid ? nu : 0) * job.rowlen) : nullptr;
+  for (int c = 0; c < nch; ++c) {
+    float re[32], im[32];
+    if (P == 2) {
+      float a[16], b[16];
+      tmem_ld16(trow + c * 16, a);
+      tmem_ld16(trow + kp + c * 16, b);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) { re[i] = a[i] * fY; im[i] = b[i] * fY; }
+    } else {
+      float a[32], b[32];
+      tmem_ld32(trow + c * 32, a);
+      tmem_ld32(trow + kp + c * 32, b);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) { re[i] = a[i] * fY; im[i] = b[i] * fY; }
+    }
+    if (!valid) continue;
+    uint4 outv[8];
+    // unweighted
+    if (rowA) {
+      if (P == 2) {
+        split8_f32(re, outv[0], outv[4]);
+        split8_f32(re + 8, outv[1], outv[5]);
+        split8_f32(im, outv[2], outv[6]);
+        split8_f32(im + 8, outv[3], outv[7]);
+      } else {
+        for (int q = 0; q < 4; ++q) outv[q] = bf16x8_f32(re + 8 * q);
+        for (int q = 0; q < 4; ++q) outv[4 + q] = bf16x8_f32(im + 8 * q);
+      }
+      uint4* dst = (uint4*)(rowA + (size_t)c * 128);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) dst[q] = outv[q];
+    }
+    if (rowB) {
+      // half-spectrum weight: 1 at omega = 0 (first element of chunk 0), else 2
+      const int gg = (P == 2) ? 16 : 32;
+      float rw[32], iw[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        if (i < gg) {
+          float w = (c == 0 && i == 0) ? 1.f : 2.f;
+          rw[i] = re[i] * w;
+          iw[i] = im[i] * w;
+        }
+      }
+      if (P == 2) {
+        split8_f32(rw, outv[0], outv[4]);
+        split8_f32(rw + 8, outv[1], outv[5]);
+        split8_f32(iw, outv[2], outv[6]);
+        split8_f32(iw + 8, outv[3], outv[7]);
+      } else {
+        for (int q = 0; q < 4; ++q) outv[q] = bf16x8_f32(rw + 8 * q);
+        for (int q = 0; q < 4; ++q) outv[4 + q] = bf16x8_f32(iw + 8 * q);
+      }
+      uint4* dst = (uint4*)(rowB + (size_t)c * 128);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) dst[q] = outv[q];
+    }
+  }
+  if (valid) {
+    double sigma = sqrt(ss / (double)(m - 1));
+    double sc;
+    if (job.alpha > 0.0)
+      sc = (sigma == 0.0) ? 0.0 : pow(sigma, -job.alpha);
+    else
+      sc = 1.0;
+    job.scale[nu] = (float)ldexp(sc, -(ey + eY));
+    if (job.sigma_out) job.sigma_out[nu] = (float)sigma;
+  }
+  if (t == 0 && !ok) {  // abort: let started copies and MMAs finish
+    if (w_armed > 0) mbar_wait_drain(wbar, (w_armed - 1) & 1, limit_ns);
+    if (m_committed > 0) mbar_wait_drain(mbar, (m_committed - 1) & 1, limit_ns);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+  (void)lane;
+}
+
+static size_t prep_smem_bytes(int planes, int max_kp) {
+  size_t bytes = 1024 + (size_t)planes * PREP_ROWS * 128 + (size_t)planes * 2 * max_kp * 128 + 64;
+  // Keep (CTAs per SM) x (TMEM columns per CTA) <= 512 so allocation never waits.
+  uint32_t cols = 32;
+  while ((int)cols < 2 * max_kp) cols <<= 1;
+  const size_t sm_smem = 233472;  // shared memory per SM
+  const size_t max_cta = 512 / cols;
+  const size_t floor_bytes = sm_smem / (max_cta + 1) + 1024;
+  return bytes > floor_bytes ? bytes : floor_bytes;
+}
+
+cudaError_t launch_prep_tc(const PrepJob* d_jobs, const PrepItem* d_items, int nitems, int planes,
+                           int max_kp, int* err, unsigned long long limit_ns, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  size_t smem = prep_smem_bytes(planes, max_kp);
+  if (planes == 2)
+    k_prep_tc<2><<<nitems, 128, smem, s>>>(d_jobs, d_items, err, limit_ns);
+  else
+    k_prep_tc<1><<<nitems, 128, smem, s>>>(d_jobs, d_items, err, limit_ns);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP32 CUDA-core DFT (the plain GPU baseline).  One CTA per 32 variables, 8
+// warps; lane = variable, warps stride over frequencies.  FP64 reference and
+// centering, then FP32 values in shared memory and FP32 twiddles indexed by
+// (omega j) mod m.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_prep_simt(SimtPrepJob job) {
+  extern __shared__ float sm[];
+  const int m = job.m, n = job.n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nu = blockIdx.x * 32 + lane;
+  const bool valid = nu < n;
+  float* tw = sm;              // 2m
+  float* yt = sm + 2 * m;      // m x 32 centred values
+  double* red = (double*)(yt + (size_t)m * 32);  // 8 x 32 partial sums
+  for (int i = threadIdx.x; i < 2 * m; i += blockDim.x) tw[i] = job.tw[i];
+  // reference (FP64)
+  double part = 0.0;
+  if (!job.ref && valid)
+    for (int j = warp; j < m; j += 8) part += (double)job.y[(long)j * job.ld + nu];
+  red[warp * 32 + lane] = part;
+  __syncthreads();
+  double ref;
+  if (job.ref) {
+    ref = valid ? (double)job.ref[nu] : 0.0;
+  } else {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w * 32 + lane];
+    ref = s / (double)m;
+  }
+  __syncthreads();
+  part = 0.0;
+  for (int j = warp; j < m; j += 8) {
+    double d = valid ? (double)job.y[(long)j * job.ld + nu] - ref : 0.0;
+    part += d * d;
+    yt[(size_t)j * 32 + lane] = (float)d;
+  }
+  red[warp * 32 + lane] = part;
+  __syncthreads();
+  if (warp == 0 && valid) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w * 32 + lane];
+    double sigma = sqrt(s / (double)(m - 1));
+    double sc = (job.alpha > 0.0) ? (sigma == 0.0 ? 0.0 : pow(sigma, -job.alpha)) : 1.0;
+    job.scale[nu] = (float)sc;
+    if (job.sigma_out) job.sigma_out[nu] = (float)sigma;
+  }
+  for (int w = warp; w < job.kp1; w += 8) {
+    float re = 0.f, im = 0.f;
+    int r = 0;  // (w * j) mod m, advanced incrementally
+    for (int j = 0; j < m; ++j) {
+      float d = yt[(size_t)j * 32 + lane];
+      re = fmaf(d, tw[2 * r], re);
+      im = fmaf(-d, tw[2 * r + 1], im);
+      r += w;
+      if (r >= m) r -= m;
+    }
+    if (valid) {
+      if (job.yr) {
+        job.yr[(size_t)w * n + nu] = re;
+        job.yi[(size_t)w * n + nu] = im;
+      }
+      if (job.yrw) {
+        float wt = (w == 0) ? 1.f : 2.f;
+        job.yrw[(size_t)w * n + nu] = wt * re;
+        job.yiw[(size_t)w * n + nu] = wt * im;
+      }
+    }
+  }
+}
+
+static size_t simt_prep_smem_bytes(int m) {
+  return (size_t)2 * m * 4 + (size_t)m * 32 * 4 + 8 * 32 * 8;
+}
+
+cudaError_t init_prep_kernels() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_prep_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_prep_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_prep_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+}
+
+cudaError_t launch_prep_simt(const SimtPrepJob& job, cudaStream_t s) {
+  size_t smem = simt_prep_smem_bytes(job.m);
+  if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
+  k_prep_simt<<<(job.n + 31) / 32, 256, smem, s>>>(job);
+  return cudaGetLastError();
+}
+
+}  // namespace c2d

@@ -1,0 +1,288 @@
+// Complex cross-spectrum on tcgen05 tensor cores (Eq. disint2d with the
+// half-spectrum weights of Sec. 4.2):
+//   Phi(nu1, nu2) = norm s1[nu1] s2[nu2] sum_w w (Re1 Re2 + Im1 Im2)
+//   Psi(nu1, nu2) = norm s1[nu1] s2[nu2] sum_w w (Im1 Re2 - Re1 Im2)
+// The weight w is already in the stack-2 operand rows; s1, s2 carry
+// sigma^-alpha and the power-of-two operand scaling.
+//
+// Persistent, warp-specialised kernel, one CTA per SM, 192 threads:
+//   warp 0      TMA producer: operand chunks of stack 1 (128 rows) and
+//               stack 2 (128 rows) into a 4-stage shared-memory ring
+//   warp 1      MMA issuer (one thread): per chunk, Phi and Psi accumulate in
+//               TMEM (128 lanes x 128 columns each); the Re*Im term of Psi
+//               uses the instruction's negate-A bit.  With FP16 hi/lo planes
+//               the products are hi*hi + hi*lo + lo*hi.
+//   warps 2..5  epilogue: TMEM -> registers, scale, 128-byte-swizzled
+//               staging tile, TMA store of 32x32 FP32 boxes; for homo
+//               problems the mirrored tile is stored too (Phi symmetric,
+//               Psi antisymmetric), so only tiles with ti <= tj are computed.
+// TMEM holds two accumulator sets (2 x 256 columns): the MMAs of tile i+1
+// run while the epilogue of tile i streams its stores.
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace c2d {
+
+constexpr int XS_STAGES = 4;
+constexpr int XS_STAGE_BYTES = 2 * TILE_M * 128;  // A chunk + B chunk
+constexpr int XS_EPI_WARPS = 4;
+constexpr int XS_EPI_BUFS = 4;                    // staging boxes per epilogue warp
+constexpr int XS_BOX_BYTES = 32 * 32 * 4;
+constexpr int XS_THREADS = 64 + 32 * XS_EPI_WARPS;
+constexpr size_t XS_SMEM = 1024 + (size_t)XS_STAGES * XS_STAGE_BYTES +
+                           (size_t)XS_EPI_WARPS * XS_EPI_BUFS * XS_BOX_BYTES + 256;
+
+template <int P>
+__device__ __forceinline__ void issue_chunk_mmas(uint32_t d_phi, uint32_t d_psi, uint32_t a0,
+                                                 uint32_t b0, uint32_t acc, uint32_t ID,
+                                                 uint32_t IDN) {
+  // ID / IDN: M = 128, N = bn, FP16 (split planes) or BF16, IDN with negate-A.
+  if (P == 2) {
+    // chunk bytes: Re_hi @0, Im_hi @32, Re_lo @64, Im_lo @96 (16 frequencies each)
+    mma_f16(d_phi, sw128_desc(a0 + 0), sw128_desc(b0 + 0), ID, acc);     // Rh Rh
+    mma_f16(d_phi, sw128_desc(a0 + 32), sw128_desc(b0 + 32), ID, 1);     // Ih Ih
+    mma_f16(d_phi, sw128_desc(a0 + 0), sw128_desc(b0 + 64), ID, 1);      // Rh Rl
+    mma_f16(d_phi, sw128_desc(a0 + 32), sw128_desc(b0 + 96), ID, 1);     // Ih Il
+    mma_f16(d_phi, sw128_desc(a0 + 64), sw128_desc(b0 + 0), ID, 1);      // Rl Rh
+    mma_f16(d_phi, sw128_desc(a0 + 96), sw128_desc(b0 + 32), ID, 1);     // Il Ih
+    mma_f16(d_psi, sw128_desc(a0 + 32), sw128_desc(b0 + 0), ID, acc);    // Ih Rh
+    mma_f16(d_psi, sw128_desc(a0 + 0), sw128_desc(b0 + 32), IDN, 1);     // -Rh Ih
+    mma_f16(d_psi, sw128_desc(a0 + 32), sw128_desc(b0 + 64), ID, 1);     // Ih Rl
+    mma_f16(d_psi, sw128_desc(a0 + 0), sw128_desc(b0 + 96), IDN, 1);     // -Rh Il
+    mma_f16(d_psi, sw128_desc(a0 + 96), sw128_desc(b0 + 0), ID, 1);      // Il Rh
+    mma_f16(d_psi, sw128_desc(a0 + 64), sw128_desc(b0 + 32), IDN, 1);    // -Rl Ih
+  } else {
+    // chunk bytes: Re @0 (two K=16 steps: 0, 32), Im @64 (64, 96)
+    mma_f16(d_phi, sw128_desc(a0 + 0), sw128_desc(b0 + 0), ID, acc);
+    mma_f16(d_phi, sw128_desc(a0 + 32), sw128_desc(b0 + 32), ID, 1);
+    mma_f16(d_phi, sw128_desc(a0 + 64), sw128_desc(b0 + 64), ID, 1);
+    mma_f16(d_phi, sw128_desc(a0 + 96), sw128_desc(b0 + 96), ID, 1);
+    mma_f16(d_psi, sw128_desc(a0 + 64), sw128_desc(b0 + 0), ID, acc);
+    mma_f16(d_psi, sw128_desc(a0 + 96), sw128_desc(b0 + 32), ID, 1);
+    mma_f16(d_psi, sw128_desc(a0 + 0), sw128_desc(b0 + 64), IDN, 1);
+    mma_f16(d_psi, sw128_desc(a0 + 32), sw128_desc(b0 + 96), IDN, 1);
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(XS_THREADS, 1)
+    k_xspec_tc(const XProblem* __restrict__ probs, const XItem* __restrict__ items, int nitems,
+               int* err, unsigned long long limit_ns) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* stages = base;
+  uint8_t* epi = base + XS_STAGES * XS_STAGE_BYTES;
+  uint64_t* bars = (uint64_t*)(epi + XS_EPI_WARPS * XS_EPI_BUFS * XS_BOX_BYTES);
+  // bars: full[S], empty[S], tfull[2], tempty[2]
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * XS_STAGES + 4);
+  auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
+  auto empty_bar = [&](int s) { return smem_u32(&bars[XS_STAGES + s]); };
+  auto tfull_bar = [&](int b) { return smem_u32(&bars[2 * XS_STAGES + b]); };
+  auto tempty_bar = [&](int b) { return smem_u32(&bars[2 * XS_STAGES + 2 + b]); };
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const WaitCtl wc{err, limit_ns};
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < XS_STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), XS_EPI_WARPS);
+    }
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int armed[XS_STAGES];
+      uint32_t armed_phase[XS_STAGES];
+      for (int s = 0; s < XS_STAGES; ++s) armed[s] = 0, armed_phase[s] = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+        const XItem w = items[it];
+        const XProblem* pr = probs + w.prob;
+        const int nch = pr->nchunks;
+        const int bn = pr->bn;
+        for (int c = 0; c < nch; ++c) {
+          if (!mbar_wait(empty_bar(stage), phase ^ 1u, wc)) { ok = false; break; }
+          mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(TILE_M + bn) * 128u);
+          armed[stage] = 1;
+          armed_phase[stage] = phase;
+          const uint32_t sa = smem_u32(stages + stage * XS_STAGE_BYTES);
+          tma_load_2d(sa, &pr->tmA, c * CHUNK_ELEMS, (int)w.ti * TILE_M, full_bar(stage));
+          tma_load_2d(sa + TILE_M * 128, &pr->tmB, c * CHUNK_ELEMS, (int)w.tj * bn,
+                      full_bar(stage));
+          if (++stage == XS_STAGES) { stage = 0; phase ^= 1u; }
+        }
+      }
+      // every load this thread started has landed before shared memory is released
+      for (int s = 0; s < XS_STAGES; ++s)
+        if (armed[s]) mbar_wait_drain(full_bar(s), armed_phase[s], limit_ns);
+    }
+  } else if (warp == 1) {
+    // ----------------------------------------------------------------- MMA
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int lt = 0, committed = 0;
+      uint32_t last_bar = 0, last_parity = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++lt) {
+        const XItem w = items[it];
+        const int nch = probs[w.prob].nchunks;
+        const int bn = probs[w.prob].bn;
+        const uint32_t id = idesc_f16(128, bn, P == 1, false);
+        const uint32_t idn = idesc_f16(128, bn, P == 1, true);
+        const int buf = lt & 1;
+        const uint32_t tpar = (uint32_t)(lt >> 1) & 1u;
+        if (!mbar_wait(tempty_bar(buf), tpar ^ 1u, wc)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d_phi = tmem + (uint32_t)buf * 256u;
+        const uint32_t d_psi = d_phi + 128u;
+        for (int c = 0; c < nch; ++c) {
+          if (!mbar_wait(full_bar(stage), phase, wc)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(stages + stage * XS_STAGE_BYTES);
+          issue_chunk_mmas<P>(d_phi, d_psi, a0, a0 + TILE_M * 128, c > 0 ? 1u : 0u, id, idn);
+          mma_commit(empty_bar(stage));
+          ++committed;
+          last_bar = empty_bar(stage);
+          last_parity = phase;
+          if (++stage == XS_STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        mma_commit(tfull_bar(buf));
+      }
+      // all MMAs this thread issued complete before TMEM is released
+      if (committed > 0) mbar_wait_drain(last_bar, last_parity, limit_ns);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int ew = warp - 2;            // epilogue warp 0..3
+    const int q = warp & 3;             // TMEM lane quadrant this warp may access
+    uint8_t* ring = epi + ew * XS_EPI_BUFS * XS_BOX_BYTES;
+    int slot = 0, issued = 0;
+    int lt = 0;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++lt) {
+      const XItem w = items[it];
+      const XProblem* pr = probs + w.prob;
+      const int buf = lt & 1;
+      const uint32_t tpar = (uint32_t)(lt >> 1) & 1u;
+      if (!mbar_wait(tfull_bar(buf), tpar, wc)) break;
+      tc_fence_after();
+      const int n1 = pr->n1, n2 = pr->n2, bn = pr->bn;
+      const int row0 = (int)w.ti * TILE_M + q * 32;  // first nu1 of this warp's rows
+      const int orow0 = row0 - pr->out_row_tile0 * TILE_M;  // its output row
+      const int row = row0 + lane;
+      const float rs = (row < n1) ? pr->norm * __ldg(pr->s1 + row) : 0.f;
+      const bool mirror = pr->mirror && (w.ti != w.tj);
+      const bool rows_in = row0 < n1;
+      for (int half = 0; half < 2; ++half) {
+        const CUtensorMap* tm = half ? &pr->tmPsi : &pr->tmPhi;
+        for (int cc = 0; cc < bn / 32; ++cc) {
+          const int col0 = (int)w.tj * bn + cc * 32;
+          if (col0 >= n2) break;  // warp-uniform
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + half * 128 + cc * 32),
+                    v);
+          if (!rows_in && !mirror) continue;
+#pragma unroll
+          for (int i = 0; i < 32; i += 4) {
+            float4 s2 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (col0 + i + 3 < n2) {
+              s2 = __ldg((const float4*)(pr->s2 + col0 + i));
+            } else {
+              if (col0 + i < n2) s2.x = __ldg(pr->s2 + col0 + i);
+              if (col0 + i + 1 < n2) s2.y = __ldg(pr->s2 + col0 + i + 1);
+              if (col0 + i + 2 < n2) s2.z = __ldg(pr->s2 + col0 + i + 2);
+            }
+            v[i] = v[i] * rs * s2.x;
+            v[i + 1] = v[i + 1] * rs * s2.y;
+            v[i + 2] = v[i + 2] * rs * s2.z;
+            v[i + 3] = v[i + 3] * rs * s2.w;
+          }
+          if (rows_in) {
+            // box (rows row0.., cols col0..): row = lane, 8 swizzled 16-byte chunks
+            if (issued >= XS_EPI_BUFS && lane == 0) bulk_wait_read<XS_EPI_BUFS - 1>();
+            __syncwarp();
+            uint8_t* box = ring + slot * XS_BOX_BYTES;
+#pragma unroll
+            for (int c4 = 0; c4 < 8; ++c4)
+              *(float4*)(box + sw128_off(lane, c4)) =
+                  make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+              tma_store_2d(tm, col0, orow0, smem_u32(box));
+              bulk_commit();
+            }
+            ++issued;
+            if (++slot == XS_EPI_BUFS) slot = 0;
+          }
+          if (mirror && rows_in) {
+            // transposed box (rows col0.., cols row0..): element (i, lane)
+            if (issued >= XS_EPI_BUFS && lane == 0) bulk_wait_read<XS_EPI_BUFS - 1>();
+            __syncwarp();
+            uint8_t* box = ring + slot * XS_BOX_BYTES;
+            const float sg = half ? -1.f : 1.f;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              *(float*)(box + sw128_off(i, lane >> 2) + (lane & 3) * 4) = sg * v[i];
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+              tma_store_2d(tm, row0, col0, smem_u32(box));
+              bulk_commit();
+            }
+            ++issued;
+            if (++slot == XS_EPI_BUFS) slot = 0;
+          }
+        }
+      }
+      // this tile's accumulators are consumed: hand the TMEM buffer back
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar(buf));
+    }
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, 512);
+}
+
+static_assert(XS_SMEM <= (size_t)kMaxDynSmem, "cross-spectrum shared memory exceeds the limit");
+
+cudaError_t init_xspec_kernels() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_xspec_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XS_SMEM)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_xspec_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XS_SMEM);
+}
+
+cudaError_t launch_xspec_tc(const XProblem* d_probs, const XItem* d_items, int nitems, int planes,
+                            int grid, int* err, unsigned long long limit_ns, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  if (grid > nitems) grid = nitems;
+  if (planes == 2)
+    k_xspec_tc<2><<<grid, XS_THREADS, XS_SMEM, s>>>(d_probs, d_items, nitems, err, limit_ns);
+  else
+    k_xspec_tc<1><<<grid, XS_THREADS, XS_SMEM, s>>>(d_probs, d_items, nitems, err, limit_ns);
+  return cudaGetLastError();
+}
+
+}  // namespace c2d

@@ -1,0 +1,281 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle.
+
+Tolerances (relative Frobenius error of Phi and of Psi separately, on the same
+seeded FP32 inputs): 1e-5 for FP32 and the FP16 hi/lo split, 1e-2 for plain
+BF16 operands.  Max-abs error is reported in the assertion messages.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "split": 1e-5, "bf16": 1e-2}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1808_00685_gb300 as pkg
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.load()
+    c = pkg.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
+
+
+def check(phi, psi, ophi, opsi, tol, what=""):
+    ep, eq = rel(phi, ophi), rel(psi, opsi)
+    mp, mq = np.abs(phi - ophi).max(), np.abs(psi - opsi).max()
+    msg = f"{what}: rel Phi {ep:.3e} Psi {eq:.3e}; max-abs Phi {mp:.3e} Psi {mq:.3e}"
+    assert ep <= tol and eq <= tol, msg
+    return ep, eq
+
+
+def run(ctx, y1, y2=None, **kw):
+    phi, psi = ctx.compute(dev(y1), None if y2 is None else dev(y2), **kw)
+    ctx.synchronize()
+    return host(phi), host(psi)
+
+
+# -------------------------------------------------------------- paper configs
+
+@pytest.mark.parametrize("prec", ["split", "bf16", "fp32"])
+def test_c1_small_homo(ctx, prec):
+    y = workloads.c1()
+    phi, psi = run(ctx, y, precision=prec)
+    ophi, opsi, _, _ = oracle.corr2d(y)
+    check(phi, psi, ophi, opsi, TOL[prec], f"c1 {prec}")
+
+
+@pytest.mark.parametrize("prec", ["split", "fp32"])
+def test_c2_homo_offset_baseline(ctx, prec):
+    """m=64, n=4096, baseline offset 10: FP64 centering on the GPU."""
+    y = workloads.c2()
+    phi, psi = run(ctx, y, precision=prec)
+    ophi, opsi, _, _ = oracle.corr2d(y, nthreads=oracle.max_threads())
+    check(phi, psi, ophi, opsi, TOL[prec], f"c2 {prec}")
+    # exact symmetry from the mirrored tiles
+    assert np.array_equal(phi, phi.T) and np.array_equal(psi, -psi.T)
+
+
+def test_c3_hetero_with_preprocessing(ctx):
+    """Raw spectra on non-uniform axes -> uniform grids -> hetero, alpha = 0.5."""
+    raw = workloads.c3()
+    y1g, _ = ctx.preprocess(dev(raw.x1), dev(raw.y1), raw.n1_out)
+    y2g, _ = ctx.preprocess(dev(raw.x2), dev(raw.y2), raw.n2_out)
+    ctx.synchronize()
+    o1, _ = oracle.interp_linear(raw.x1, raw.y1, raw.n1_out)
+    o2, _ = oracle.interp_linear(raw.x2, raw.y2, raw.n2_out)
+    # interpolation: the correctly rounded FP32 value of the FP64 blend, bit for bit
+    assert np.array_equal(y1g.cpu().numpy(), o1.astype(np.float32))
+    assert np.array_equal(y2g.cpu().numpy(), o2.astype(np.float32))
+    rows = workloads.sample_rows(raw.n1_out, 512, seed=31)
+    phi, psi = ctx.compute(y1g, y2g, precision="split", alpha=raw.alpha)
+    ctx.synchronize()
+    ophi, opsi, _, _ = oracle.corr2d(o1.astype(np.float32), o2.astype(np.float32),
+                                     alpha=raw.alpha, rows=rows, nthreads=oracle.max_threads())
+    check(host(phi)[rows], host(psi)[rows], ophi, opsi, 1e-5, "c3 split sampled rows")
+
+
+def test_c4_full_size_sampled_rows(ctx):
+    """m=256, n=32768 (8.6 GB of output) in split precision; 256 sampled rows."""
+    y = workloads.c4()
+    yd = dev(y)
+    phi, psi = ctx.compute(yd, precision="split")
+    ctx.synchronize()
+    rows = workloads.sample_rows(y.shape[1], 256, seed=41)
+    rt = torch.from_numpy(rows.astype(np.int64)).cuda()
+    gphi = host(phi.index_select(0, rt))
+    gpsi = host(psi.index_select(0, rt))
+    del phi, psi
+    torch.cuda.empty_cache()
+    ophi, opsi, _, _ = oracle.corr2d(y, rows=rows, nthreads=oracle.max_threads())
+    check(gphi, gpsi, ophi, opsi, 1e-5, "c4 split sampled rows")
+    # mirrored columns: Phi(j, i) = Phi(i, j) at sampled rows i
+    assert np.all(np.isfinite(gphi))
+
+
+# ----------------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("m,n", [(2, 1), (2, 7), (3, 33), (4, 129), (5, 128), (16, 257),
+                                 (65, 300), (130, 131), (257, 140), (512, 64)])
+@pytest.mark.parametrize("prec", ["split", "fp32"])
+def test_ragged_and_extreme_shapes(ctx, m, n, prec):
+    y = workloads.random_stack(m, n, seed=m * 1000 + n, offset=3.0)
+    phi, psi = run(ctx, y, precision=prec)
+    ophi, opsi, _, _ = oracle.corr2d(y)
+    if np.linalg.norm(ophi) == 0:  # m = 2: only the DC term, zero after centering
+        assert np.abs(phi).max() < 1e-6 and np.abs(psi).max() < 1e-6
+        return
+    check(phi, psi, ophi, opsi, TOL[prec], f"m={m} n={n} {prec}")
+
+
+@pytest.mark.parametrize("prec", ["split", "bf16", "fp32"])
+def test_hetero_uneven(ctx, prec):
+    y1 = workloads.random_stack(37, 300, seed=1, offset=-2.0)
+    y2 = workloads.random_stack(37, 170, seed=2, offset=5.0)
+    phi, psi = run(ctx, y1, y2, precision=prec)
+    ophi, opsi, _, _ = oracle.corr2d(y1, y2)
+    check(phi, psi, ophi, opsi, TOL[prec], f"hetero {prec}")
+
+
+@pytest.mark.parametrize("prec", ["split", "fp32"])
+def test_user_reference_norm_and_scaling(ctx, prec):
+    y1 = workloads.random_stack(20, 200, seed=3)
+    y2 = workloads.random_stack(20, 150, seed=4)
+    r1, r2 = y1[0].copy(), y2[-1].copy()
+    phi, psi = run(ctx, y1, y2, precision=prec, ref1=dev(r1), ref2=dev(r2), norm=0.5, alpha=1.0)
+    ophi, opsi, _, _ = oracle.corr2d(y1, y2, ref1=r1, ref2=r2, norm=0.5, alpha=1.0)
+    check(phi, psi, ophi, opsi, TOL[prec], f"user ref {prec}")
+
+
+def test_constant_variable_gives_zero_rows(ctx):
+    y = workloads.random_stack(9, 140, seed=5)
+    y[:, 17] = 2.5
+    for prec in ("split", "fp32"):
+        phi, psi = run(ctx, y, precision=prec, alpha=0.5)
+        assert np.all(phi[17] == 0) and np.all(phi[:, 17] == 0) and np.all(psi[17] == 0)
+        assert np.all(np.isfinite(phi)) and np.all(np.isfinite(psi))
+        ophi, opsi, _, _ = oracle.corr2d(y, alpha=0.5)
+        check(phi, psi, ophi, opsi, TOL[prec], f"sigma=0 {prec}")
+
+
+def test_sigma_outputs_and_padded_leading_dimensions(ctx):
+    import paper_1808_00685_gb300 as pkg
+    m, n = 24, 150
+    y = workloads.random_stack(m, n, seed=6, offset=1.0)
+    ypad = np.zeros((m, 160), np.float32)
+    ypad[:, :n] = y
+    yd = dev(ypad)[:, :n]  # leading dimension 160
+    phi, psi, ldo = pkg.Context.alloc_out(n, n, yd.device, ld=164)
+    ph, ps, s1, s2 = ctx.compute(yd, out=(phi, psi), want_sigma=True)
+    ctx.synchronize()
+    ophi, opsi, os1, _ = oracle.corr2d(y)
+    check(host(ph)[:, :n], host(ps)[:, :n], ophi, opsi, 1e-5, "padded ld")
+    assert np.allclose(s1.cpu().numpy(), os1, rtol=1e-6)
+
+
+def test_mirror_and_full_tiles_agree(ctx):
+    y = workloads.random_stack(40, 400, seed=7)
+    a = run(ctx, y, precision="split")
+    b = run(ctx, y, precision="split", no_mirror=True)
+    ophi, opsi, _, _ = oracle.corr2d(y)
+    check(*a, ophi, opsi, 1e-5, "mirror")
+    check(*b, ophi, opsi, 1e-5, "no mirror")
+
+
+def test_self_hetero_matches_homo(ctx):
+    y = workloads.random_stack(30, 260, seed=8)
+    a = run(ctx, y, precision="split", no_mirror=True)
+    b = run(ctx, y, y.copy(), precision="split")
+    assert rel(a[0], b[0]) < 1e-6 and rel(a[1], b[1]) < 1e-6
+
+
+# ------------------------------------------------------------ preprocessing
+
+def test_preprocess_reference_subtraction_bit_exact(ctx):
+    rng = np.random.default_rng(9)
+    x = workloads.jittered_axis(777, 0.0, 500.0, rng)
+    y = workloads.random_stack(13, 777, seed=10)
+    ref = workloads.random_stack(1, 600, seed=11)[0]
+    out, dyn = ctx.preprocess(dev(x), dev(y), 600, ref=dev(ref))
+    ctx.synchronize()
+    o, od = oracle.interp_linear(x, y, 600, ref=ref)
+    assert np.array_equal(out.cpu().numpy(), o.astype(np.float32))
+    assert np.array_equal(dyn.cpu().numpy(), od.astype(np.float32))
+
+
+def test_preprocess_rejects_non_increasing_axis(ctx):
+    import paper_1808_00685_gb300 as pkg
+    x = np.linspace(0, 1, 50)
+    x[20] = x[19]
+    y = workloads.random_stack(3, 50, seed=1)
+    ctx.preprocess(dev(x), dev(y), 40)
+    with pytest.raises(pkg.Corr2dError) as ei:
+        ctx.synchronize()
+    assert ei.value.status == pkg.EINVAL
+    ctx.synchronize()  # the error word was cleared
+
+
+# --------------------------------------------------------------- ABI errors
+
+def test_invalid_arguments_return_status(ctx):
+    import paper_1808_00685_gb300 as pkg
+    y = dev(workloads.random_stack(8, 64, seed=1))
+    with pytest.raises(pkg.Corr2dError) as ei:
+        ctx.compute(y[:1])  # m = 1
+    assert ei.value.status == pkg.EINVAL
+    phi = torch.empty((64, 66), device="cuda")
+    with pytest.raises(pkg.Corr2dError) as ei:  # ldo % 4 != 0 for TMA stores
+        ctx.compute(y, out=(phi, phi.clone()))
+    assert ei.value.status == pkg.EINVAL
+    with pytest.raises(pkg.Corr2dError) as ei:  # host stack
+        hy = workloads.random_stack(8, 64, seed=1)
+        p = pkg.make_params()
+        out = torch.empty((64, 64), device="cuda")
+        pkg.corr2d_compute(ctx.handle, 8, 64, hy.ctypes.data, 64, 0, None, 0, p, out.data_ptr(),
+                           out.data_ptr(), 64)
+    assert ei.value.status == pkg.EINVAL
+    with pytest.raises(pkg.Corr2dError) as ei:  # m beyond the tensor-core limit
+        ctx.compute(dev(workloads.random_stack(513, 16, seed=2)))
+    assert ei.value.status == pkg.EUNSUPPORTED
+    ctx.synchronize()
+
+
+def test_fp32_path_accepts_large_m(ctx):
+    y = workloads.random_stack(600, 70, seed=12)
+    phi, psi = run(ctx, y, precision="fp32")
+    ophi, opsi, _, _ = oracle.corr2d(y)
+    check(phi, psi, ophi, opsi, 1e-5, "fp32 m=600")
+
+
+# -------------------------------------------------------------------- batch
+
+def test_batch_matches_oracle_and_single_calls(ctx):
+    import paper_1808_00685_gb300 as pkg
+    spec = workloads.c5_spec(count=10, seed=5, m_lo=8, m_hi=200, n_lo=40, n_hi=700)
+    inputs = workloads.batch_inputs(spec, nbands=5)
+    probs, outs = [], []
+    for (y1, y2), p in zip(inputs, spec.problems):
+        d1 = dev(y1)
+        d2 = None if y2 is None else dev(y2)
+        phi, psi, ldo = pkg.Context.alloc_out(p.n1, p.n2, d1.device)
+        probs.append((d1, d2, phi, psi))
+        outs.append((phi, psi))
+    for rep in range(2):  # second call replays the captured graph
+        ctx.batch(probs, precision="split")
+        ctx.synchronize()
+        for (y1, y2), p, (phi, psi) in zip(inputs, spec.problems, outs):
+            ophi, opsi, _, _ = oracle.corr2d(y1, y2)
+            check(host(phi)[:, :p.n2], host(psi)[:, :p.n2], ophi, opsi, 1e-5,
+                  f"batch m={p.m} n1={p.n1} n2={p.n2} homo={p.homo}")
+
+
+def test_host_buffer_entry_point(ctx):
+    y1 = workloads.random_stack(33, 300, seed=13)
+    y2 = workloads.random_stack(33, 260, seed=14)
+    phi, psi = ctx.compute_host(torch.from_numpy(y1), torch.from_numpy(y2))
+    ophi, opsi, _, _ = oracle.corr2d(y1, y2)
+    check(phi.double().numpy(), psi.double().numpy(), ophi, opsi, 1e-5, "host buffers")
+    phi, psi = ctx.compute_host(torch.from_numpy(y1))
+    ophi, opsi, _, _ = oracle.corr2d(y1)
+    check(phi.double().numpy(), psi.double().numpy(), ophi, opsi, 1e-5, "host buffers homo")
