@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark of the generalized 2D correlation hot path on GB300.
+
+Default workload: homo correlation, m = 256 perturbation steps, n = 32768
+spectral variables, FP16 hi/lo split precision (32768^2 complex outputs,
+8.6 GB of Phi and Psi per step).  A step is one corr2d_compute call: FP64
+reference/centering/sigma + tcgen05 DFT kernel, then the tcgen05
+cross-spectrum kernel.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c4|c2|c3|c5] [--precision split|bf16|fp32]
+
+Under torchrun each rank runs its own independent problem on its own GPU
+(weak scaling, no data-path collective); the reported value is all ranks'
+outputs divided by the slowest rank's time.  --impl reference times the FP64
+CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2D-corr output elems/s & % HBM roofline, split-prec vs FP32 at 1e-5 rel err"
+UNIT = "output elems/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["c4", "c2", "c3", "c5"], default="c4")
+    ap.add_argument("--precision", choices=["split", "bf16", "fp32"], default="split")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-n", type=int, default=0,
+                    help="spectral variables of the oracle sample (0: sized to ~10-30 s)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- workloads
+def workload(name, precision):
+    """(description dict, inputs) for a workload name."""
+    import workloads as wl
+    if name == "c4":
+        y = wl.c4()
+        return dict(workload=f"homo m=256 n=32768 {precision}", m=256, n1=32768, n2=32768,
+                    homo=True, alpha=0.0, precision=precision), (y, None)
+    if name == "c2":
+        y = wl.c2()
+        return dict(workload=f"homo m=64 n=4096 {precision}", m=64, n1=4096, n2=4096, homo=True,
+                    alpha=0.0, precision=precision), (y, None)
+    if name == "c3":
+        raw = wl.c3()
+        return dict(workload=f"hetero m=128 n1=8192 n2=2048 alpha=0.5 {precision} "
+                             f"(with preprocessing)", m=128, n1=8192, n2=2048, homo=False,
+                    alpha=0.5, precision=precision), raw
+    spec = wl.c5_spec()
+    return dict(workload=f"batched 512 problems m~U[8,200] n log-uniform [256,8192] {precision}",
+                problems=len(spec.problems), outputs=spec.total_outputs, precision=precision,
+                alpha=0.0), spec
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def xspec_traffic_per_launch(workload_name, precision):
+    """DRAM bytes of one cross-spectrum launch from the committed ncu summary, if that
+    summary was taken on the current kernel source (same sha256), else None."""
+    src = os.path.join(ROOT, "paper_1808_00685_gb300", "csrc", "k_xspec.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    summ = os.path.join(ROOT, "profiles", f"xspec_{workload_name}_{precision}.md")
+    if not os.path.exists(summ):
+        return None
+    text = open(summ).read()
+    m_sha = re.search(r"k_xspec\.cu sha256:\s*([0-9a-f]{64})", text)
+    m_b = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != sha:
+        return None
+    return float(m_b.group(1))
+
+
+def rowlen_elems(m, precision):
+    planes = 2 if precision == "split" else 1
+    g = 16 if planes == 2 else 32
+    kp = ((m - 1) // 2 + 1 + g - 1) // g * g
+    return kp // g * 64
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def reduce_max(pg, value, device):
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_oracle_rate(y, n_sample=0, alpha=0.0, target_s=15.0):
+    """The FP64 oracle as it stands, all host threads, on the first n_sample
+    spectral variables of the same stack (homo).  Returns (elems/s, info)."""
+    import oracle
+    threads = oracle.max_threads()
+    m = y.shape[0]
+    if n_sample <= 0:
+        # calibrate on a small sample, then size the run to ~15 s
+        n0 = 256
+        t0 = time.perf_counter()
+        oracle.corr2d(y[:, :n0].copy(), alpha=alpha, nthreads=threads)
+        dt = max(time.perf_counter() - t0, 1e-3)
+        n_sample = int(min(y.shape[1], max(n0, n0 * (target_s / dt) ** 0.5)))
+    ys = y[:, :n_sample].copy()
+    t0 = time.perf_counter()
+    oracle.corr2d(ys, alpha=alpha, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return n_sample * n_sample / dt, dict(
+        kind="oracle", cores=threads,
+        sample=f"homo m={m}, first {n_sample} spectral variables of the same stack "
+               f"({n_sample * n_sample} outputs, {dt:.1f} s)", seconds=dt)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local, pg):
+    import numpy as np
+    import torch
+
+    import paper_1808_00685_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(device)
+    desc, inputs = workload(args.workload, args.precision)
+    ctx = pkg.Context(local, stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    launches_per_step = 2
+
+    if args.workload in ("c4", "c2"):
+        y, _ = inputs
+        yd = torch.from_numpy(y).to(device)
+        m, n = y.shape
+        phi, psi, ldo = pkg.Context.alloc_out(n, n, device)
+        outputs = n * n
+
+        def step():
+            ctx.compute(yd, precision=args.precision, out=(phi, psi))
+        xbytes = 8.0 * n * n + 2.0 * n * rowlen_elems(m, args.precision) * 2
+    elif args.workload == "c3":
+        raw = inputs
+        x1, y1r = torch.from_numpy(raw.x1).to(device), torch.from_numpy(raw.y1).to(device)
+        x2, y2r = torch.from_numpy(raw.x2).to(device), torch.from_numpy(raw.y2).to(device)
+        n1, n2 = raw.n1_out, raw.n2_out
+        phi, psi, ldo = pkg.Context.alloc_out(n1, n2, device)
+        outputs = n1 * n2
+
+        def step():
+            a, _ = ctx.preprocess(x1, y1r, n1)
+            b, _ = ctx.preprocess(x2, y2r, n2)
+            ctx.compute(a, b, precision=args.precision, alpha=raw.alpha, out=(phi, psi))
+        launches_per_step = 6  # 2 x (axis check + interpolation), DFT, cross-spectrum
+        xbytes = 8.0 * n1 * n2 + 2.0 * (n1 + n2) * rowlen_elems(128, args.precision)
+        y = raw.y1
+    else:
+        spec = inputs
+        import workloads as wl
+        ins = wl.batch_inputs(spec)
+        probs = []
+        for (y1, y2), p in zip(ins, spec.problems):
+            d1 = torch.from_numpy(y1).to(device)
+            d2 = None if y2 is None else torch.from_numpy(y2).to(device)
+            ph, ps, _ = pkg.Context.alloc_out(p.n1, p.n2, device)
+            probs.append((d1, d2, ph, ps))
+        outputs = spec.total_outputs
+
+        def step():
+            ctx.batch(probs, precision=args.precision)
+        xbytes = 8.0 * outputs
+        y = None
+
+    ctx.set_profiling(True)
+    for _ in range(max(args.warmup, 0)):
+        step()
+    ctx.synchronize()
+    torch.cuda.synchronize()
+    barrier(pg)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    barrier(pg)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    prep_ms, xspec_ms = [], []
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush, outside the step's events
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        p_ms, x_ms = ctx.timings()  # waits for this step's kernel events
+        prep_ms.append(p_ms)
+        xspec_ms.append(x_ms)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    clocks = sampler.stop()
+    ctx.synchronize()  # raises on a device-side time-out
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(step_ms)
+    ms_max = reduce_max(pg, ms, device)
+    value = world * outputs / (ms_max / 1e3)
+
+    peak, peak_kind = measured_peaks()
+    x_mean = statistics.mean(xspec_ms)
+    achieved = xbytes / (x_mean / 1e3) / 1e9
+    traffic = xspec_traffic_per_launch(args.workload, args.precision)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "k_xspec_tc" if args.precision != "fp32" else "k_xspec_simt",
+                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": xbytes,
+                "kernel_ms": round(x_mean, 4), "prep_ms": round(statistics.mean(prep_ms), 4)}
+    if args.precision == "fp32":
+        roofline["bound"] = "alu"
+        fp32_peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
+        kp1 = (desc.get("m", 2) - 1) // 2 + 1
+        n_ = desc.get("n1", 0)
+        # 8 flops per output and frequency, unique outputs of a homo problem
+        flops = 8.0 * kp1 * (n_ * (n_ + 1) / 2 if desc.get("homo") else outputs)
+        ach = flops / (x_mean / 1e3) / 1e12
+        roofline.update({"achieved": round(ach, 2), "peak": round(fp32_peak_tflops, 1),
+                         "unit": "TFLOP/s", "frac": round(ach / fp32_peak_tflops, 4),
+                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"})
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e and args.workload in ("c4", "c2"):
+        y_h = torch.from_numpy(y).pin_memory()
+        phi_h = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        psi_h = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        ctx.compute_host(y_h, precision=args.precision, out=(phi_h, psi_h))  # warm-up
+        times = []
+        for _ in range(max(args.e2e_steps, 1)):
+            t0 = time.perf_counter()
+            ctx.compute_host(y_h, precision=args.precision, out=(phi_h, psi_h))
+            times.append(time.perf_counter() - t0)
+        e2e_s = reduce_max(pg, statistics.mean(times), device)
+        e2e = {"value": world * outputs / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(y.nbytes), "d2h_bytes_per_step": int(2 * n * n * 4),
+               "api": "corr2d_compute_host", "ms_per_step": round(e2e_s * 1e3, 2)}
+        del phi_h, psi_h, y_h
+
+    ctx.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and y is not None:
+        rate, info = cpu_oracle_rate(y, args.cpu_sample_n, desc.get("alpha", 0.0))
+        cpu = {"value": rate, "unit": UNIT, **{k: v for k, v in info.items() if k != "seconds"}}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"split": "f16 hi/lo split, f32 accumulate (f64 centering)",
+                  "bf16": "bf16, f32 accumulate (f64 centering)",
+                  "fp32": "f32 (f64 centering)"}[args.precision],
+        "data": "synthetic (seeded band spectra; the paper's datasets are not available)",
+        "config": {**desc, "l2": "flushed before every timed step (256 MB write outside the "
+                                 "step's events); each step writes >= 134 MB of output",
+                   "parallelism": f"weak: one independent problem per GPU x{world}"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": launches_per_step * args.steps,
+        "region_ms": round(r0.elapsed_time(r1), 3),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    desc, inputs = workload(args.workload if args.workload != "c5" else "c4", args.precision)
+    if args.workload in ("c4", "c2"):
+        y = inputs[0]
+    elif args.workload == "c3":
+        y = inputs.y1
+    else:
+        y = inputs[0]
+    import oracle
+    rates = []
+    n_s = args.cpu_sample_n or 0
+    info = None
+    ms = []
+    target = max(2.0, min(15.0, 150.0 / max(args.steps, 1)))
+    for _ in range(max(args.steps, 1)):
+        rate, info = cpu_oracle_rate(y, n_s, desc.get("alpha", 0.0), target)
+        n_s = int(re.search(r"first (\d+)", info["sample"]).group(1))
+        rates.append(rate)
+        ms.append(info["seconds"] * 1e3)
+    value = statistics.mean(rates)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(statistics.mean(ms), 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded band spectra; the paper's datasets are not available)",
+        "config": desc, "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": info["kind"],
+                         "cores": info["cores"], "sample": info["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        # each step is one bounded oracle sample; keep the whole run to a few minutes
+        if args.cpu_sample_n <= 0:
+            args.cpu_sample_n = 0
+        run_reference(args, world, rank)
+        return
+    world, rank, local, pg = dist_setup(args)
+    try:
+        run_ours(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

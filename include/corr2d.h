@@ -185,6 +185,16 @@ typedef struct {
 corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* host_problems,
                            const corr2d_params* shared_params);
 
+/* Per-kernel timing of the last corr2d_compute / corr2d_batch call on this
+ * context, from CUDA events recorded on the context's stream around each
+ * kernel while profiling is on (the paper profiles its own steps the same
+ * way, Sec. 4.3).  corr2d_get_timings waits for those events.
+ *   prep_ms   reference, centering, sigma and DFT kernel(s)
+ *   xspec_ms  cross-spectrum kernel
+ * Returns EINVAL when profiling is off or nothing was recorded yet. */
+corr2d_status corr2d_set_profiling(corr2d_ctx* ctx, int on);
+corr2d_status corr2d_get_timings(corr2d_ctx* ctx, float* prep_ms, float* xspec_ms);
+
 /* Library version string. */
 const char* corr2d_version(void);
 

@@ -35,7 +35,8 @@ _PREC_BY_NAME = {"fp32": PREC_FP32, "split": PREC_SPLIT, "bf16": PREC_BF16}
 EXPORTED_SYMBOLS = (
     "corr2d_params_default", "corr2d_create", "corr2d_destroy", "corr2d_set_stream",
     "corr2d_last_error", "corr2d_synchronize", "corr2d_preprocess", "corr2d_compute",
-    "corr2d_compute_host", "corr2d_batch", "corr2d_version",
+    "corr2d_compute_host", "corr2d_batch", "corr2d_version", "corr2d_set_profiling",
+    "corr2d_get_timings",
 )
 
 
@@ -87,6 +88,9 @@ def load(path: str | None = None):
             "corr2d_batch": (i, [vp, i, ctypes.POINTER(corr2d_problem),
                                  ctypes.POINTER(corr2d_params)]),
             "corr2d_version": (ctypes.c_char_p, []),
+            "corr2d_set_profiling": (i, [vp, i]),
+            "corr2d_get_timings": (i, [vp, ctypes.POINTER(ctypes.c_float),
+                                       ctypes.POINTER(ctypes.c_float)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -159,6 +163,16 @@ def corr2d_version() -> str:
     return load().corr2d_version().decode()
 
 
+def corr2d_set_profiling(ctx: int, on: bool) -> None:
+    _check(ctx, load().corr2d_set_profiling(ctx, 1 if on else 0))
+
+
+def corr2d_get_timings(ctx: int):
+    a, b = ctypes.c_float(), ctypes.c_float()
+    _check(ctx, load().corr2d_get_timings(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 # ------------------------------------------------------------ torch helpers
 def _ptr(t):
     return None if t is None else t.data_ptr()
@@ -208,6 +222,13 @@ class Context:
 
     def synchronize(self):
         corr2d_synchronize(self.handle)
+
+    def set_profiling(self, on: bool = True):
+        corr2d_set_profiling(self.handle, on)
+
+    def timings(self):
+        """(prep_ms, xspec_ms) of the last call (profiling must be on)."""
+        return corr2d_get_timings(self.handle)
 
     @staticmethod
     def alloc_out(n1, n2, device, ld=None):

@@ -74,6 +74,9 @@ struct corr2d_ctx {
   DevBuf host_in;   // corr2d_compute_host: stacks
   DevBuf host_out;  // corr2d_compute_host: two slab pairs
   bool fault_alloc = false;
+  bool profiling = false;
+  bool recorded = false;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // before prep, between, after xspec
 };
 
 namespace {
@@ -369,13 +372,19 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
                 skip_prep ? std::vector<PrepItem>{} : pitems, probs, xitems);
   if ((st = upload_blob(ctx, descbuf, desc_last, b)) != CORR2D_OK) return st;
   uint8_t* d = (uint8_t*)descbuf.p;
+  if (ctx->profiling) cudaEventRecord(ctx->ev[0], ctx->stream);
   if (!skip_prep)
     CUDA_TRY(ctx, launch_prep_tc((const PrepJob*)(d + b.off_jobs),
                                  (const PrepItem*)(d + b.off_pitems), b.npitems, pl.planes, pl.kp,
                                  ctx->d_err, ctx->limit_ns, ctx->stream));
+  if (ctx->profiling) cudaEventRecord(ctx->ev[1], ctx->stream);
   CUDA_TRY(ctx, launch_xspec_tc((const XProblem*)(d + b.off_probs),
                                 (const XItem*)(d + b.off_xitems), b.nxitems, pl.planes,
                                 ctx->sm_count, ctx->d_err, ctx->limit_ns, ctx->stream));
+  if (ctx->profiling) {
+    cudaEventRecord(ctx->ev[2], ctx->stream);
+    ctx->recorded = true;
+  }
   return CORR2D_OK;
 }
 
@@ -402,6 +411,7 @@ corr2d_status enqueue_simt(corr2d_ctx* ctx, int m, int n1, const float* y1, int 
   j.ref = p.ref_mode == CORR2D_REF_USER ? p.ref1 : nullptr;
   j.yr = yr1; j.yi = yi1; j.scale = s1; j.sigma_out = sig1;
   j.yrw = homo ? yr2 : nullptr; j.yiw = homo ? yi2 : nullptr;
+  if (ctx->profiling) cudaEventRecord(ctx->ev[0], ctx->stream);
   CUDA_TRY(ctx, launch_prep_simt(j, ctx->stream));
   if (!homo) {
     SimtPrepJob k = j;
@@ -412,8 +422,13 @@ corr2d_status enqueue_simt(corr2d_ctx* ctx, int m, int n1, const float* y1, int 
   }
   const float norm = (float)(p.norm > 0.0 ? p.norm : 1.0 / (kPi * (double)(m - 1)));
   const bool mirror = homo && !(p.flags & CORR2D_FLAG_NO_MIRROR);
+  if (ctx->profiling) cudaEventRecord(ctx->ev[1], ctx->stream);
   CUDA_TRY(ctx, launch_xspec_simt(kp1, n1, homo ? n1 : n2, yr1, yi1, yr2, yi2, s1, s2, norm, phi,
                                   psi, ldo, mirror, ctx->stream));
+  if (ctx->profiling) {
+    cudaEventRecord(ctx->ev[2], ctx->stream);
+    ctx->recorded = true;
+  }
   return CORR2D_OK;
 }
 
@@ -507,6 +522,9 @@ corr2d_status corr2d_create(corr2d_ctx** out, int device, void* cuda_stream) {
   if (init_prep_kernels() != cudaSuccess || init_xspec_kernels() != cudaSuccess)
     return fail(nullptr, CORR2D_ECUDA, "kernel attribute setup failed: %s",
                 cudaGetErrorString(cudaGetLastError()));
+  for (int i = 0; i < 3; ++i)
+    if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess)
+      return fail(nullptr, CORR2D_ECUDA, "cannot create timing events");
   if (cudaMalloc(&ctx->d_err, 256) != cudaSuccess)
     return fail(nullptr, CORR2D_ENOMEM, "cannot allocate the error word");
   if (cudaMemset(ctx->d_err, 0, 256) != cudaSuccess)
@@ -534,6 +552,8 @@ corr2d_status corr2d_destroy(corr2d_ctx* ctx) {
   for (auto& kv : ctx->twiddles) release(kv.second);
   for (auto& kv : ctx->simt_tw) release(kv.second);
   if (ctx->d_err) cudaFree(ctx->d_err);
+  for (int i = 0; i < 3; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   delete ctx;
   return CORR2D_OK;
 }
@@ -541,6 +561,27 @@ corr2d_status corr2d_destroy(corr2d_ctx* ctx) {
 corr2d_status corr2d_set_stream(corr2d_ctx* ctx, void* cuda_stream) {
   if (!ctx) return CORR2D_EINVAL;
   ctx->stream = (cudaStream_t)cuda_stream;
+  return CORR2D_OK;
+}
+
+corr2d_status corr2d_set_profiling(corr2d_ctx* ctx, int on) {
+  if (!ctx) return CORR2D_EINVAL;
+  ctx->profiling = on != 0;
+  ctx->recorded = false;
+  return CORR2D_OK;
+}
+
+corr2d_status corr2d_get_timings(corr2d_ctx* ctx, float* prep_ms, float* xspec_ms) {
+  if (!ctx) return CORR2D_EINVAL;
+  if (!ctx->profiling || !ctx->recorded)
+    return fail(ctx, CORR2D_EINVAL, "no timings recorded (profiling off or no call yet)");
+  DeviceGuard g(ctx->device);
+  CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev[2]));
+  float a = 0.f, b = 0.f;
+  CUDA_TRY(ctx, cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]));
+  CUDA_TRY(ctx, cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]));
+  if (prep_ms) *prep_ms = a;
+  if (xspec_ms) *xspec_ms = b;
   return CORR2D_OK;
 }
 
@@ -805,6 +846,7 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
   BatchCache& bc = ctx->batch;
   if (bc.exec && bc.key == key) {
     CUDA_TRY(ctx, cudaGraphLaunch(bc.exec, ctx->stream));
+    ctx->recorded = ctx->profiling;
     ctx->err.clear();
     return CORR2D_OK;
   }
@@ -902,10 +944,14 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
     CUDA_TRY(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph;
     CUDA_TRY(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    // event nodes inside the graph give per-kernel timings when profiling is on
+    cudaEventRecord(ctx->ev[0], cs);
     cudaError_t e1 = launch_prep_tc((const PrepJob*)(d + b.off_jobs), (const PrepItem*)(d + b.off_pitems),
                                     b.npitems, planes, max_kp, ctx->d_err, ctx->limit_ns, cs);
+    cudaEventRecord(ctx->ev[1], cs);
     cudaError_t e2 = launch_xspec_tc((const XProblem*)(d + b.off_probs), (const XItem*)(d + b.off_xitems),
                                      b.nxitems, planes, ctx->sm_count, ctx->d_err, ctx->limit_ns, cs);
+    cudaEventRecord(ctx->ev[2], cs);
     cudaError_t e3 = cudaStreamEndCapture(cs, &graph);
     cudaStreamDestroy(cs);
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
@@ -945,6 +991,7 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
   if ((st = make_graph(best_thr, &bc.exec)) != CORR2D_OK) return st;
   bc.key = key;
   CUDA_TRY(ctx, cudaGraphLaunch(bc.exec, ctx->stream));
+  ctx->recorded = ctx->profiling;
   ctx->err.clear();
   return CORR2D_OK;
 }

@@ -92,19 +92,39 @@ __global__ void __launch_bounds__(256) k_xspec_simt(int kp1, int n1, int n2,
       ap[i][j] = ap[i][j] * rsc[i] * csc[j];
       aq[i][j] = aq[i][j] * rsc[i] * csc[j];
     }
+  // On a diagonal homo tile, 8x8 block (ty, tx) with tx > ty writes itself and
+  // its mirror, tx == ty writes its upper triangle and mirrors it, tx < ty is
+  // left to block (tx, ty): the output is exactly (anti)symmetric.
+  const bool diag = mirror && ti == tj;
+  if (diag && tx < ty) return;
+  const bool tri = diag && tx == ty;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int r = r0 + i;
     if (r >= n1) break;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      if (c0 + j < n2) {
+      if (c0 + j < n2 && (!tri || j >= i)) {
         phi[(size_t)r * ldo + c0 + j] = ap[i][j];
-        psi[(size_t)r * ldo + c0 + j] = aq[i][j];
+        psi[(size_t)r * ldo + c0 + j] = (tri && j == i) ? 0.f : aq[i][j];
       }
     }
   }
-  if (mirror && ti != tj) {
+  if (tri) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int r = c0 + j;
+      if (r >= n2) break;
+#pragma unroll
+      for (int i = 0; i < j; ++i) {
+        if (r0 + i < n1) {
+          phi[(size_t)r * ldo + r0 + i] = ap[i][j];
+          psi[(size_t)r * ldo + r0 + i] = -aq[i][j];
+        }
+      }
+    }
+  }
+  if (mirror && !tri) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int r = c0 + j;  // mirrored row

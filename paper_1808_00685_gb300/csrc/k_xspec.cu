@@ -189,13 +189,22 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
       const int orow0 = row0 - pr->out_row_tile0 * TILE_M;  // its output row
       const int row = row0 + lane;
       const float rs = (row < n1) ? pr->norm * __ldg(pr->s1 + row) : 0.f;
-      const bool mirror = pr->mirror && (w.ti != w.tj);
+      // Homo tiles off the diagonal store themselves and their mirror.  On a
+      // diagonal tile, 32x32 box (q, cc) with cc > q stores itself and its
+      // mirror, cc == q stores its upper triangle and mirrors it into the
+      // lower one, cc < q is left to box (cc, q): the output is then exactly
+      // symmetric (Phi) / antisymmetric with zero diagonal (Psi).
+      const bool diag = pr->mirror && (w.ti == w.tj);
       const bool rows_in = row0 < n1;
       for (int half = 0; half < 2; ++half) {
         const CUtensorMap* tm = half ? &pr->tmPsi : &pr->tmPhi;
+        const float sg = half ? -1.f : 1.f;
         for (int cc = 0; cc < bn / 32; ++cc) {
           const int col0 = (int)w.tj * bn + cc * 32;
           if (col0 >= n2) break;  // warp-uniform
+          if (diag && cc < q) continue;
+          const bool mirror = pr->mirror && (!diag || cc > q);
+          const bool tri = diag && cc == q;
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + half * 128 + cc * 32),
                     v);
@@ -220,10 +229,23 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
             if (issued >= XS_EPI_BUFS && lane == 0) bulk_wait_read<XS_EPI_BUFS - 1>();
             __syncwarp();
             uint8_t* box = ring + slot * XS_BOX_BYTES;
+            if (!tri) {
 #pragma unroll
-            for (int c4 = 0; c4 < 8; ++c4)
-              *(float4*)(box + sw128_off(lane, c4)) =
-                  make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+              for (int c4 = 0; c4 < 8; ++c4)
+                *(float4*)(box + sw128_off(lane, c4)) =
+                    make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+            } else {
+              // element (lane, c) for c >= lane, its mirror (c, lane) for c > lane
+#pragma unroll
+              for (int c = 0; c < 32; ++c) {
+                if (c > lane) {
+                  *(float*)(box + sw128_off(lane, c >> 2) + (c & 3) * 4) = v[c];
+                  *(float*)(box + sw128_off(c, lane >> 2) + (lane & 3) * 4) = sg * v[c];
+                } else if (c == lane) {
+                  *(float*)(box + sw128_off(lane, c >> 2) + (c & 3) * 4) = half ? 0.f : v[c];
+                }
+              }
+            }
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) {
@@ -238,7 +260,6 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
             if (issued >= XS_EPI_BUFS && lane == 0) bulk_wait_read<XS_EPI_BUFS - 1>();
             __syncwarp();
             uint8_t* box = ring + slot * XS_BOX_BYTES;
-            const float sg = half ? -1.f : 1.f;
 #pragma unroll
             for (int i = 0; i < 32; ++i)
               *(float*)(box + sw128_off(i, lane >> 2) + (lane & 3) * 4) = sg * v[i];
