@@ -195,6 +195,45 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hos
 corr2d_status corr2d_set_profiling(corr2d_ctx* ctx, int on);
 corr2d_status corr2d_get_timings(corr2d_ctx* ctx, float* prep_ms, float* xspec_ms);
 
+/*
+ * Allocation-free variant of corr2d_compute.  The paper has no counterpart:
+ * this entry point exists for callers of this library that must not allocate
+ * GPU memory -- a program whose memory planner already owns the whole device,
+ * a plugin whose host framework forbids hidden allocations, a latency-critical
+ * loop that cannot pay the implicit synchronisation of cudaMalloc/cudaFree,
+ * or code without a library context (corr2d_create allocates).
+ *
+ * It takes no context.  The caller passes the device, a stream (cudaStream_t,
+ * NULL = legacy default stream), the stacks and the Phi/Psi outputs exactly as
+ * for corr2d_compute (device memory of `device`; ldo % 4 == 0; 16-byte
+ * aligned outputs).  All intermediates live in one static device array of
+ * CORR2D_NOALLOC_SCRATCH_BYTES that the library declares; every GPU that
+ * loads the library keeps that array until the process exits.  The call
+ * allocates no device memory: no cudaMalloc, no cudaFree, no allocating
+ * library routine.
+ *
+ * - Precisions: CORR2D_PREC_SPLIT and CORR2D_PREC_BF16 (FP32: EUNSUPPORTED).
+ * - Size limit: a problem needs about (n1 + n2) * rowbytes + twiddles, with
+ *   rowbytes = 1 KB for m <= 257 in SPLIT (2 KB for m <= 513); anything larger
+ *   than the array returns EUNSUPPORTED with the byte counts in `msg`, before
+ *   any work is enqueued.  Example: homo n = 8000 at m = 256 fits.
+ * - The first call on a device does a one-time set-up there (it looks up the
+ *   array's device address with cudaGetSymbolAddress and sets kernel
+ *   attributes); make that first call before any stream capture begins.
+ * - The call is synchronous: it returns after the results are in phi/psi
+ *   (it waits for `cuda_stream`) and reports CORR2D_ETIMEOUT if a device-side
+ *   wait ran out.
+ * - All calls share the one array and it keeps the last call's contents.
+ *   Calls that overlap on the GPU (from several host threads or streams) race
+ *   on it; serialise them.
+ * - msg (nullable, msg_len bytes) receives the reason for a failure.
+ */
+#define CORR2D_NOALLOC_SCRATCH_BYTES (32u << 20)
+corr2d_status corr2d_compute_noalloc(int device, void* cuda_stream, int m, int n1,
+                                     const float* y1, int ld1, int n2, const float* y2, int ld2,
+                                     const corr2d_params* params, float* phi, float* psi,
+                                     long ldo, char* msg, size_t msg_len);
+
 /* Library version string. */
 const char* corr2d_version(void);
 

@@ -36,7 +36,7 @@ EXPORTED_SYMBOLS = (
     "corr2d_params_default", "corr2d_create", "corr2d_destroy", "corr2d_set_stream",
     "corr2d_last_error", "corr2d_synchronize", "corr2d_preprocess", "corr2d_compute",
     "corr2d_compute_host", "corr2d_batch", "corr2d_version", "corr2d_set_profiling",
-    "corr2d_get_timings",
+    "corr2d_get_timings", "corr2d_compute_noalloc",
 )
 
 
@@ -88,6 +88,9 @@ def load(path: str | None = None):
             "corr2d_batch": (i, [vp, i, ctypes.POINTER(corr2d_problem),
                                  ctypes.POINTER(corr2d_params)]),
             "corr2d_version": (ctypes.c_char_p, []),
+            "corr2d_compute_noalloc": (i, [i, vp, i, i, vp, i, i, vp, i,
+                                           ctypes.POINTER(corr2d_params), vp, vp, ctypes.c_long,
+                                           ctypes.c_char_p, ctypes.c_size_t]),
             "corr2d_set_profiling": (i, [vp, i]),
             "corr2d_get_timings": (i, [vp, ctypes.POINTER(ctypes.c_float),
                                        ctypes.POINTER(ctypes.c_float)]),
@@ -161,6 +164,20 @@ def corr2d_batch(ctx, problems, params=None) -> None:
 
 def corr2d_version() -> str:
     return load().corr2d_version().decode()
+
+
+def corr2d_compute_noalloc(device, stream, m, n1, y1, ld1, n2, y2, ld2, params, phi, psi,
+                           ldo) -> None:
+    """Allocation-free correlation (no context, static device scratch; synchronous).
+
+    For callers that must not allocate GPU memory; see include/corr2d.h for
+    the size limit and the rule that calls must not overlap on the GPU."""
+    buf = ctypes.create_string_buffer(512)
+    pp = ctypes.byref(params) if params is not None else None
+    st = load().corr2d_compute_noalloc(device, stream, m, n1, y1, ld1, n2, y2, ld2, pp, phi, psi,
+                                       ldo, buf, len(buf))
+    if st != OK:
+        raise Corr2dError(st, buf.value.decode())
 
 
 def corr2d_set_profiling(ctx: int, on: bool) -> None:
