@@ -47,18 +47,23 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=0,
+                    help="c4 only: use the first N spectral variables (small profiling case)")
     ap.add_argument("--cpu-sample-n", type=int, default=0,
                     help="spectral variables of the oracle sample (0: sized to ~10-30 s)")
     return ap.parse_args()
 
 
 # ---------------------------------------------------------------- workloads
-def workload(name, precision):
+def workload(name, precision, n_override=0):
     """(description dict, inputs) for a workload name."""
     import workloads as wl
     if name == "c4":
         y = wl.c4()
-        return dict(workload=f"homo m=256 n=32768 {precision}", m=256, n1=32768, n2=32768,
+        if n_override and n_override < y.shape[1]:
+            y = y[:, :n_override].copy()
+        n = y.shape[1]
+        return dict(workload=f"homo m=256 n={n} {precision}", m=256, n1=n, n2=n,
                     homo=True, alpha=0.0, precision=precision), (y, None)
     if name == "c2":
         y = wl.c2()
@@ -199,12 +204,17 @@ def cpu_oracle_rate(y, n_sample=0, alpha=0.0, target_s=15.0):
     threads = oracle.max_threads()
     m = y.shape[0]
     if n_sample <= 0:
-        # calibrate on a small sample, then size the run to ~15 s
-        n0 = 256
-        t0 = time.perf_counter()
-        oracle.corr2d(y[:, :n0].copy(), alpha=alpha, nthreads=threads)
-        dt = max(time.perf_counter() - t0, 1e-3)
-        n_sample = int(min(y.shape[1], max(n0, n0 * (target_s / dt) ** 0.5)))
+        # the oracle costs a n (its DFT) + b n^2 (the correlation): calibrate
+        # on two small samples, then size the measured run to ~target_s
+        ts = []
+        for n0 in (256, 1024):
+            t0 = time.perf_counter()
+            oracle.corr2d(y[:, :n0].copy(), alpha=alpha, nthreads=threads)
+            ts.append(max(time.perf_counter() - t0, 1e-4))
+        b = max((ts[1] / 1024 - ts[0] / 256) / (1024 - 256), 1e-15)
+        a = max(ts[0] / 256 - b * 256, 0.0)
+        n_est = (-a + math.sqrt(a * a + 4 * b * target_s)) / (2 * b)
+        n_sample = int(min(y.shape[1], max(256, n_est)))
     ys = y[:, :n_sample].copy()
     t0 = time.perf_counter()
     oracle.corr2d(ys, alpha=alpha, nthreads=threads)
@@ -225,7 +235,7 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     stream = torch.cuda.current_stream(device)
-    desc, inputs = workload(args.workload, args.precision)
+    desc, inputs = workload(args.workload, args.precision, args.n)
     ctx = pkg.Context(local, stream)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
     launches_per_step = 2

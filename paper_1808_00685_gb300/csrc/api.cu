@@ -74,6 +74,7 @@ struct corr2d_ctx {
   DevBuf host_in;   // corr2d_compute_host: stacks
   DevBuf host_out;  // corr2d_compute_host: two slab pairs
   bool fault_alloc = false;
+  int fault_inject = 0;  // CORR2D_FAULT=stall: the cross-spectrum producer never arrives
   bool profiling = false;
   bool recorded = false;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // before prep, between, after xspec
@@ -380,7 +381,8 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   if (ctx->profiling) cudaEventRecord(ctx->ev[1], ctx->stream);
   CUDA_TRY(ctx, launch_xspec_tc((const XProblem*)(d + b.off_probs),
                                 (const XItem*)(d + b.off_xitems), b.nxitems, pl.planes,
-                                ctx->sm_count, ctx->d_err, ctx->limit_ns, ctx->stream));
+                                ctx->sm_count, ctx->d_err, ctx->limit_ns, ctx->stream,
+                                ctx->fault_inject));
   if (ctx->profiling) {
     cudaEventRecord(ctx->ev[2], ctx->stream);
     ctx->recorded = true;
@@ -533,7 +535,10 @@ corr2d_status corr2d_create(corr2d_ctx** out, int device, void* cuda_stream) {
     long v = atol(lim);
     if (v > 0) ctx->limit_ns = (unsigned long long)v * 1000000ull;
   }
-  if (const char* f = getenv("CORR2D_FAULT")) ctx->fault_alloc = (strcmp(f, "alloc") == 0);
+  if (const char* f = getenv("CORR2D_FAULT")) {
+    ctx->fault_alloc = (strcmp(f, "alloc") == 0);
+    ctx->fault_inject = (strcmp(f, "stall") == 0) ? 1 : 0;
+  }
   *out = ctx.release();
   return CORR2D_OK;
 }

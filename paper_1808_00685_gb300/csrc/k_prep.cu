@@ -133,30 +133,41 @@ __global__ void __launch_bounds__(128) k_prep_tc(const PrepJob* __restrict__ job
   // ---- 1. FP64 reference, sums of squares and range (Eqs. ref, dynspec, stdev)
   const float* y = job.y;
   const long ld = job.ld;
-  double ref = 0.0;
+  // FP64 is kept to the two steps that need it (GB300's FP64 rate is low):
+  // the reference mean and the centering subtraction.  The range of y - ref
+  // comes from the FP32 extremes of y, the sum of squares from the centred
+  // FP32 values (compensated summation).
+  double ref = 0.0, amax = 0.0;
   if (valid) {
+    float ymin = y[nu], ymax = ymin;
     if (job.ref) {
+      for (int j = 1; j < m; ++j) {
+        const float v = y[(long)j * ld + nu];
+        ymin = fminf(ymin, v);
+        ymax = fmaxf(ymax, v);
+      }
       ref = (double)job.ref[nu];
     } else {
-      double s = 0.0;
-      for (int j = 0; j < m; ++j) s += (double)y[(long)j * ld + nu];
+      double s = (double)ymin;
+      for (int j = 1; j < m; ++j) {
+        const float v = y[(long)j * ld + nu];
+        s += (double)v;
+        ymin = fminf(ymin, v);
+        ymax = fmaxf(ymax, v);
+      }
       ref = s / (double)m;
     }
+    amax = fmax((double)ymax - ref, ref - (double)ymin);  // extremes of |y - ref|
   }
-  double ss = 0.0, amax = 0.0;
-  if (valid) {
-    for (int j = 0; j < m; ++j) {
-      double d = (double)y[(long)j * ld + nu] - ref;
-      ss += d * d;
-      amax = fmax(amax, fabs(d));
-    }
-  }
+  float ss = 0.f, ss_c = 0.f;  // Kahan sum of (y - ref)^2
   int ey = 0;
   if (amax > 0.0) {
     int e;
     frexp(amax, &e);  // amax < 2^e
     ey = 14 - e;      // scaled maximum in [2^13, 2^14)
+    if (ey > 126) ey = 126;  // keep 2^ey a normal FP32 number (data below ~1e-34)
   }
+  const float fy = ldexpf(1.0f, ey);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -182,20 +193,26 @@ __global__ void __launch_bounds__(128) k_prep_tc(const PrepJob* __restrict__ job
     // centred, scaled values of steps 64 kc .. 64 kc + 63 for this variable
 #pragma unroll 1
     for (int jg = 0; jg < 8; ++jg) {
-      double v[8];
+      float v[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        int j = kc * 64 + jg * 8 + e;
-        v[e] = (valid && j < m) ? ldexp((double)y[(long)j * ld + nu] - ref, ey) : 0.0;
+        const int j = kc * 64 + jg * 8 + e;
+        // FP64 centering, rounded once to FP32; scaling by 2^ey is exact
+        const float d = (valid && j < m) ? (float)((double)y[(long)j * ld + nu] - ref) : 0.f;
+        const float sq = fmaf(d, d, -ss_c);
+        const float tsum = ss + sq;
+        ss_c = (tsum - ss) - sq;
+        ss = tsum;
+        v[e] = d * fy;
       }
       uint32_t off = sw128_off((uint32_t)t, (uint32_t)jg);
       if (P == 2) {
         uint4 hi, lo;
-        split8_f64(v, hi, lo);
+        split8_f32(v, hi, lo);
         *(uint4*)(sA + off) = hi;
         *(uint4*)(sA + PREP_ROWS * 128 + off) = lo;
       } else {
-        *(uint4*)(sA + off) = bf16x8_f64(v);
+        *(uint4*)(sA + off) = bf16x8_f32(v);
       }
     }
     fence_proxy_async_smem();

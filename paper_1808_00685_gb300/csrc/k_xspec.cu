@@ -5,17 +5,18 @@
 // The weight w is already in the stack-2 operand rows; s1, s2 carry
 // sigma^-alpha and the power-of-two operand scaling.
 //
-// Persistent, warp-specialised kernel, one CTA per SM, 192 threads:
+// Persistent, warp-specialised kernel, one CTA per SM, 320 threads:
 //   warp 0      TMA producer: operand chunks of stack 1 (128 rows) and
-//               stack 2 (128 rows) into a 4-stage shared-memory ring
+//               stack 2 (bn rows) into a 4-stage shared-memory ring
 //   warp 1      MMA issuer (one thread): per chunk, Phi and Psi accumulate in
-//               TMEM (128 lanes x 128 columns each); the Re*Im term of Psi
+//               TMEM (128 lanes x bn columns each); the Re*Im term of Psi
 //               uses the instruction's negate-A bit.  With FP16 hi/lo planes
 //               the products are hi*hi + hi*lo + lo*hi.
-//   warps 2..5  epilogue: TMEM -> registers, scale, 128-byte-swizzled
-//               staging tile, TMA store of 32x32 FP32 boxes; for homo
-//               problems the mirrored tile is stored too (Phi symmetric,
-//               Psi antisymmetric), so only tiles with ti <= tj are computed.
+//   warps 2..9  epilogue, two warps per TMEM lane quadrant (one for Phi, one
+//               for Psi): TMEM -> registers, scale, 128-byte-swizzled staging
+//               box, TMA store of 32x32 FP32 boxes.  For homo problems the
+//               mirrored box is stored too (Phi symmetric, Psi antisymmetric),
+//               so only tiles with ti <= tj are computed.
 // TMEM holds two accumulator sets (2 x 256 columns): the MMAs of tile i+1
 // run while the epilogue of tile i streams its stores.
 #include "internal.h"
@@ -24,13 +25,14 @@
 namespace c2d {
 
 constexpr int XS_STAGES = 4;
-constexpr int XS_STAGE_BYTES = 2 * TILE_M * 128;  // A chunk + B chunk
-constexpr int XS_EPI_WARPS = 4;
-constexpr int XS_EPI_BUFS = 4;                    // staging boxes per epilogue warp
+constexpr int XS_STAGE_BYTES = 2 * TILE_M * 128;  // A chunk + B chunk (bn <= 128 rows)
+constexpr int XS_EPI_WARPS = 8;
 constexpr int XS_BOX_BYTES = 32 * 32 * 4;
+constexpr int XS_EPI_SLOTS = 2;                   // staging boxes per epilogue warp
 constexpr int XS_THREADS = 64 + 32 * XS_EPI_WARPS;
 constexpr size_t XS_SMEM = 1024 + (size_t)XS_STAGES * XS_STAGE_BYTES +
-                           (size_t)XS_EPI_WARPS * XS_EPI_BUFS * XS_BOX_BYTES + 256;
+                           (size_t)XS_EPI_WARPS * XS_EPI_SLOTS * XS_BOX_BYTES +
+                           (size_t)XS_EPI_WARPS * TILE_N * 4 + 256;
 
 template <int P>
 __device__ __forceinline__ void issue_chunk_mmas(uint32_t d_phi, uint32_t d_psi, uint32_t a0,
@@ -67,12 +69,13 @@ __device__ __forceinline__ void issue_chunk_mmas(uint32_t d_phi, uint32_t d_psi,
 template <int P>
 __global__ void __launch_bounds__(XS_THREADS, 1)
     k_xspec_tc(const XProblem* __restrict__ probs, const XItem* __restrict__ items, int nitems,
-               int* err, unsigned long long limit_ns) {
+               int* err, unsigned long long limit_ns, int inject) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* stages = base;
   uint8_t* epi = base + XS_STAGES * XS_STAGE_BYTES;
-  uint64_t* bars = (uint64_t*)(epi + XS_EPI_WARPS * XS_EPI_BUFS * XS_BOX_BYTES);
+  float* s2stage = (float*)(epi + XS_EPI_WARPS * XS_EPI_SLOTS * XS_BOX_BYTES);
+  uint64_t* bars = (uint64_t*)(s2stage + XS_EPI_WARPS * TILE_N);
   // bars: full[S], empty[S], tfull[2], tempty[2]
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * XS_STAGES + 4);
   auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
@@ -111,12 +114,18 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
       int armed[XS_STAGES];
       uint32_t armed_phase[XS_STAGES];
       for (int s = 0; s < XS_STAGES; ++s) armed[s] = 0, armed_phase[s] = 0;
-      bool ok = true;
+      // inject & 1: a host-requested fault for tests -- the producer issues
+      // nothing, so the MMA and epilogue waits run out and report a time-out.
+      bool ok = (inject & 1) == 0;
+      int cur_prob = -1, nch = 0, bn = 0;
       for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
         const XItem w = items[it];
         const XProblem* pr = probs + w.prob;
-        const int nch = pr->nchunks;
-        const int bn = pr->bn;
+        if (w.prob != cur_prob) {
+          cur_prob = w.prob;
+          nch = pr->nchunks;
+          bn = pr->bn;
+        }
         for (int c = 0; c < nch; ++c) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, wc)) { ok = false; break; }
           mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(TILE_M + bn) * 128u);
@@ -141,12 +150,17 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
       int lt = 0, committed = 0;
       uint32_t last_bar = 0, last_parity = 0;
       bool ok = true;
+      int cur_prob = -1, nch = 0;
+      uint32_t id = 0, idn = 0;
       for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++lt) {
         const XItem w = items[it];
-        const int nch = probs[w.prob].nchunks;
-        const int bn = probs[w.prob].bn;
-        const uint32_t id = idesc_f16(128, bn, P == 1, false);
-        const uint32_t idn = idesc_f16(128, bn, P == 1, true);
+        if (w.prob != cur_prob) {
+          cur_prob = w.prob;
+          nch = probs[w.prob].nchunks;
+          const int bn = probs[w.prob].bn;
+          id = idesc_f16(128, bn, P == 1, false);
+          idn = idesc_f16(128, bn, P == 1, true);
+        }
         const int buf = lt & 1;
         const uint32_t tpar = (uint32_t)(lt >> 1) & 1u;
         if (!mbar_wait(tempty_bar(buf), tpar ^ 1u, wc)) { ok = false; break; }
@@ -172,107 +186,120 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int ew = warp - 2;            // epilogue warp 0..3
-    const int q = warp & 3;             // TMEM lane quadrant this warp may access
-    uint8_t* ring = epi + ew * XS_EPI_BUFS * XS_BOX_BYTES;
-    int slot = 0, issued = 0;
+    const int ew = warp - 2;      // epilogue warp 0..7
+    const int half = ew >> 2;     // 0: Phi, 1: Psi
+    const int q = warp & 3;       // TMEM lane quadrant this warp may access
+    const float sg = half ? -1.f : 1.f;
+    uint8_t* slot0 = epi + ew * XS_EPI_SLOTS * XS_BOX_BYTES;
+    uint8_t* slot1 = slot0 + XS_BOX_BYTES;
+    float* s2w = s2stage + ew * TILE_N;
     int lt = 0;
+    bool pending = false;  // lane 0 has a bulk group whose smem reads may be in flight
+    int cur_prob = -1;
+    const CUtensorMap* tm = nullptr;
+    const float* s1p = nullptr;
+    const float* s2p = nullptr;
+    int n1 = 0, n2 = 0, bn = 0, pmirror = 0, orow_off = 0;
+    float norm = 0.f;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++lt) {
       const XItem w = items[it];
-      const XProblem* pr = probs + w.prob;
+      if (w.prob != cur_prob) {
+        cur_prob = w.prob;
+        const XProblem* pr = probs + w.prob;
+        tm = half ? &pr->tmPsi : &pr->tmPhi;
+        s1p = pr->s1;
+        s2p = pr->s2;
+        n1 = pr->n1;
+        n2 = pr->n2;
+        bn = pr->bn;
+        pmirror = pr->mirror;
+        orow_off = pr->out_row_tile0 * TILE_M;
+        norm = pr->norm;
+      }
+      const int row0 = (int)w.ti * TILE_M + q * 32;  // first nu1 of this warp's rows
+      const int row = row0 + lane;
+      const int colt = (int)w.tj * bn;                // first nu2 of the tile
+      // tile constants while the MMAs finish: row scale, column scales in smem
+      const float rs = (row < n1) ? norm * __ldg(s1p + row) : 0.f;
+      {
+        const int c = colt + lane * 4;
+        float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane * 4 < bn) {
+          if (c + 3 < n2) {
+            sv = __ldg((const float4*)(s2p + c));
+          } else {
+            if (c < n2) sv.x = __ldg(s2p + c);
+            if (c + 1 < n2) sv.y = __ldg(s2p + c + 1);
+            if (c + 2 < n2) sv.z = __ldg(s2p + c + 2);
+          }
+          *(float4*)(s2w + lane * 4) = sv;
+        }
+      }
+      __syncwarp();
       const int buf = lt & 1;
       const uint32_t tpar = (uint32_t)(lt >> 1) & 1u;
       if (!mbar_wait(tfull_bar(buf), tpar, wc)) break;
       tc_fence_after();
-      const int n1 = pr->n1, n2 = pr->n2, bn = pr->bn;
-      const int row0 = (int)w.ti * TILE_M + q * 32;  // first nu1 of this warp's rows
-      const int orow0 = row0 - pr->out_row_tile0 * TILE_M;  // its output row
-      const int row = row0 + lane;
-      const float rs = (row < n1) ? pr->norm * __ldg(pr->s1 + row) : 0.f;
-      // Homo tiles off the diagonal store themselves and their mirror.  On a
-      // diagonal tile, 32x32 box (q, cc) with cc > q stores itself and its
-      // mirror, cc == q stores its upper triangle and mirrors it into the
-      // lower one, cc < q is left to box (cc, q): the output is then exactly
-      // symmetric (Phi) / antisymmetric with zero diagonal (Psi).
-      const bool diag = pr->mirror && (w.ti == w.tj);
+      // Homo tiles off the diagonal store each box and its mirror.  On a
+      // diagonal tile, box (q, cc) with cc > q stores itself and its mirror,
+      // cc == q stores its upper triangle and mirrors it into the lower one,
+      // cc < q is left to box (cc, q): the output is then exactly symmetric
+      // (Phi) / antisymmetric with zero diagonal (Psi).
+      const bool diag = pmirror && (w.ti == w.tj);
       const bool rows_in = row0 < n1;
-      for (int half = 0; half < 2; ++half) {
-        const CUtensorMap* tm = half ? &pr->tmPsi : &pr->tmPhi;
-        const float sg = half ? -1.f : 1.f;
-        for (int cc = 0; cc < bn / 32; ++cc) {
-          const int col0 = (int)w.tj * bn + cc * 32;
-          if (col0 >= n2) break;  // warp-uniform
-          if (diag && cc < q) continue;
-          const bool mirror = pr->mirror && (!diag || cc > q);
-          const bool tri = diag && cc == q;
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + half * 128 + cc * 32),
-                    v);
-          if (!rows_in && !mirror) continue;
+      const int nbox = bn / 32;
+      for (int cc = diag ? q : 0; cc < nbox; ++cc) {
+        const int col0 = colt + cc * 32;
+        if (col0 >= n2) break;  // warp-uniform
+        const bool mirror = pmirror && (!diag || cc > q);
+        const bool tri = diag && cc == q;
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + half * 128 + cc * 32),
+                  v);
+        if (!rows_in) continue;  // rows beyond n1 (their mirror columns are beyond n2 too)
 #pragma unroll
-          for (int i = 0; i < 32; i += 4) {
-            float4 s2 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (col0 + i + 3 < n2) {
-              s2 = __ldg((const float4*)(pr->s2 + col0 + i));
-            } else {
-              if (col0 + i < n2) s2.x = __ldg(pr->s2 + col0 + i);
-              if (col0 + i + 1 < n2) s2.y = __ldg(pr->s2 + col0 + i + 1);
-              if (col0 + i + 2 < n2) s2.z = __ldg(pr->s2 + col0 + i + 2);
-            }
-            v[i] = v[i] * rs * s2.x;
-            v[i + 1] = v[i + 1] * rs * s2.y;
-            v[i + 2] = v[i + 2] * rs * s2.z;
-            v[i + 3] = v[i + 3] * rs * s2.w;
-          }
-          if (rows_in) {
-            // box (rows row0.., cols col0..): row = lane, 8 swizzled 16-byte chunks
-            if (issued >= XS_EPI_BUFS && lane == 0) bulk_wait_read<XS_EPI_BUFS - 1>();
-            __syncwarp();
-            uint8_t* box = ring + slot * XS_BOX_BYTES;
-            if (!tri) {
+        for (int i = 0; i < 32; i += 4) {
+          const float4 s4 = *(const float4*)(s2w + cc * 32 + i);
+          v[i] = v[i] * rs * s4.x;
+          v[i + 1] = v[i + 1] * rs * s4.y;
+          v[i + 2] = v[i + 2] * rs * s4.z;
+          v[i + 3] = v[i + 3] * rs * s4.w;
+        }
+        // the previous group's reads of both slots must be complete
+        if (pending && lane == 0) bulk_wait_read<0>();
+        __syncwarp();
+        if (!tri) {
+          // box (rows row0.., cols col0..): row = lane, 8 swizzled 16-byte chunks
 #pragma unroll
-              for (int c4 = 0; c4 < 8; ++c4)
-                *(float4*)(box + sw128_off(lane, c4)) =
-                    make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
-            } else {
-              // element (lane, c) for c >= lane, its mirror (c, lane) for c > lane
-#pragma unroll
-              for (int c = 0; c < 32; ++c) {
-                if (c > lane) {
-                  *(float*)(box + sw128_off(lane, c >> 2) + (c & 3) * 4) = v[c];
-                  *(float*)(box + sw128_off(c, lane >> 2) + (lane & 3) * 4) = sg * v[c];
-                } else if (c == lane) {
-                  *(float*)(box + sw128_off(lane, c >> 2) + (c & 3) * 4) = half ? 0.f : v[c];
-                }
-              }
-            }
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-              tma_store_2d(tm, col0, orow0, smem_u32(box));
-              bulk_commit();
-            }
-            ++issued;
-            if (++slot == XS_EPI_BUFS) slot = 0;
-          }
-          if (mirror && rows_in) {
+          for (int c4 = 0; c4 < 8; ++c4)
+            *(float4*)(slot0 + sw128_off(lane, c4)) =
+                make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+          if (mirror) {
             // transposed box (rows col0.., cols row0..): element (i, lane)
-            if (issued >= XS_EPI_BUFS && lane == 0) bulk_wait_read<XS_EPI_BUFS - 1>();
-            __syncwarp();
-            uint8_t* box = ring + slot * XS_BOX_BYTES;
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-              *(float*)(box + sw128_off(i, lane >> 2) + (lane & 3) * 4) = sg * v[i];
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-              tma_store_2d(tm, row0, col0, smem_u32(box));
-              bulk_commit();
+              *(float*)(slot1 + sw128_off(i, lane >> 2) + (lane & 3) * 4) = sg * v[i];
+          }
+        } else {
+          // element (lane, c) for c >= lane, its mirror (c, lane) for c > lane
+#pragma unroll
+          for (int c = 0; c < 32; ++c) {
+            if (c > lane) {
+              *(float*)(slot0 + sw128_off(lane, c >> 2) + (c & 3) * 4) = v[c];
+              *(float*)(slot0 + sw128_off(c, lane >> 2) + (lane & 3) * 4) = sg * v[c];
+            } else if (c == lane) {
+              *(float*)(slot0 + sw128_off(lane, c >> 2) + (c & 3) * 4) = half ? 0.f : v[c];
             }
-            ++issued;
-            if (++slot == XS_EPI_BUFS) slot = 0;
           }
         }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          tma_store_2d(tm, col0, row0 - orow_off, smem_u32(slot0));
+          if (mirror && !tri) tma_store_2d(tm, row0, col0, smem_u32(slot1));
+          bulk_commit();
+        }
+        pending = true;
       }
       // this tile's accumulators are consumed: hand the TMEM buffer back
       tc_fence_before();
@@ -296,13 +323,14 @@ cudaError_t init_xspec_kernels() {
 }
 
 cudaError_t launch_xspec_tc(const XProblem* d_probs, const XItem* d_items, int nitems, int planes,
-                            int grid, int* err, unsigned long long limit_ns, cudaStream_t s) {
+                            int grid, int* err, unsigned long long limit_ns, cudaStream_t s,
+                            int inject) {
   if (nitems <= 0) return cudaSuccess;
   if (grid > nitems) grid = nitems;
   if (planes == 2)
-    k_xspec_tc<2><<<grid, XS_THREADS, XS_SMEM, s>>>(d_probs, d_items, nitems, err, limit_ns);
+    k_xspec_tc<2><<<grid, XS_THREADS, XS_SMEM, s>>>(d_probs, d_items, nitems, err, limit_ns, inject);
   else
-    k_xspec_tc<1><<<grid, XS_THREADS, XS_SMEM, s>>>(d_probs, d_items, nitems, err, limit_ns);
+    k_xspec_tc<1><<<grid, XS_THREADS, XS_SMEM, s>>>(d_probs, d_items, nitems, err, limit_ns, inject);
   return cudaGetLastError();
 }
 
