@@ -75,6 +75,11 @@ typedef enum {
  * tile and its mirror (Phi symmetric, Psi antisymmetric: Sec. 3 and Sec. 4.3).
  * This flag forces every tile to be computed instead. */
 #define CORR2D_FLAG_NO_MIRROR 1u
+/* Homo correlation: the tile tuner may pick full (unmirrored) tiles when they
+ * are faster; the result then agrees with the mirrored one to rounding but is
+ * not bit-for-bit symmetric.  This flag keeps the mirrored tiles, so Phi is
+ * exactly symmetric and Psi exactly antisymmetric with a zero diagonal. */
+#define CORR2D_FLAG_EXACT_SYMMETRY 2u
 
 typedef struct {
   int ref_mode;       /* corr2d_ref_mode */

@@ -43,6 +43,7 @@ struct DevBuf {
 struct TileChoice {
   int bn = 128;
   int mirror = 1;
+  int group = 0;  // tile order: 0 row-major, G > 0: G x G tile super-blocks
 };
 
 struct BatchCache {
@@ -234,12 +235,26 @@ corr2d_status encode_output(corr2d_ctx* ctx, CUtensorMap* tm, float* base, int r
 }
 
 // Tile list of one problem, appended to `items`.
+// The persistent kernel hands out items in list order, so items that are
+// close in the list run at the same time on different SMs.  Row-major order
+// makes concurrent tiles share output rows; G x G super-blocks make them share
+// both rows and columns, which keeps the mirrored stores of homo tiles in
+// fewer DRAM pages.
 void append_tiles(std::vector<XItem>& items, int prob, int n1, int n2, int bn, bool mirror,
-                  int ti_begin, int ti_end) {
+                  int ti_begin, int ti_end, int group = 0) {
+  (void)n1;
   const int nt2 = (n2 + bn - 1) / bn;
-  for (int ti = ti_begin; ti < ti_end; ++ti)
-    for (int tj = mirror ? ti : 0; tj < nt2; ++tj)
-      items.push_back(XItem{prob, (uint16_t)ti, (uint16_t)tj});
+  if (group <= 0) {
+    for (int ti = ti_begin; ti < ti_end; ++ti)
+      for (int tj = mirror ? ti : 0; tj < nt2; ++tj)
+        items.push_back(XItem{prob, (uint16_t)ti, (uint16_t)tj});
+    return;
+  }
+  for (int bi = ti_begin; bi < ti_end; bi += group)
+    for (int bj = mirror ? (bi - ti_begin) / group * group + ti_begin : 0; bj < nt2; bj += group)
+      for (int ti = bi; ti < std::min(bi + group, ti_end); ++ti)
+        for (int tj = std::max(bj, mirror ? ti : 0); tj < std::min(bj + group, nt2); ++tj)
+          items.push_back(XItem{prob, (uint16_t)ti, (uint16_t)tj});
 }
 
 // Host descriptor blob: [PrepJob...][PrepItem...][XProblem...][XItem...], each 128-aligned.
@@ -368,7 +383,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   xp.out_row_tile0 = out_row_tile0;
   std::vector<XProblem> probs{xp};
   std::vector<XItem> xitems;
-  append_tiles(xitems, 0, n1, n2, tc.bn, xp.mirror != 0, ti_begin, ti_end);
+  append_tiles(xitems, 0, n1, n2, tc.bn, xp.mirror != 0, ti_begin, ti_end, tc.group);
   Blob b = pack(skip_prep ? std::vector<PrepJob>{} : jobs,
                 skip_prep ? std::vector<PrepItem>{} : pitems, probs, xitems);
   if ((st = upload_blob(ctx, descbuf, desc_last, b)) != CORR2D_OK) return st;
@@ -673,13 +688,23 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
                                   float* phi, float* psi, long ldo, TileChoice* out) {
   const bool homo = (y2 == nullptr);
   const int n2e = homo ? n1 : n2;
-  auto key = std::make_tuple(m, n1, n2e, homo ? 1 : 0, p.precision * 2 + ((p.flags & CORR2D_FLAG_NO_MIRROR) ? 1 : 0));
+  auto key = std::make_tuple(m, n1, n2e, homo ? 1 : 0,
+                             p.precision * 4 + (int)(p.flags & (CORR2D_FLAG_NO_MIRROR |
+                                                                CORR2D_FLAG_EXACT_SYMMETRY)));
   auto it = ctx->tuned.find(key);
   if (it != ctx->tuned.end()) { *out = it->second; return CORR2D_OK; }
   std::vector<TileChoice> cands;
-  if (homo && !(p.flags & CORR2D_FLAG_NO_MIRROR)) cands.push_back(TileChoice{128, 1});
-  cands.push_back(TileChoice{128, 0});
-  cands.push_back(TileChoice{64, 0});
+  const bool can_mirror = homo && !(p.flags & CORR2D_FLAG_NO_MIRROR);
+  if (can_mirror) {  // every mirrored order gives bit-identical, exactly symmetric output
+    cands.push_back(TileChoice{128, 1, 0});
+    cands.push_back(TileChoice{128, 1, 8});
+    cands.push_back(TileChoice{128, 1, 12});
+  }
+  if (!(can_mirror && (p.flags & CORR2D_FLAG_EXACT_SYMMETRY))) {
+    cands.push_back(TileChoice{128, 0, 0});
+    cands.push_back(TileChoice{128, 0, 12});
+    cands.push_back(TileChoice{64, 0, 0});
+  }
   if (getenv("CORR2D_NO_TUNE") || cands.size() == 1) {
     *out = cands[0];
     ctx->tuned[key] = *out;
@@ -705,6 +730,9 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
       cudaEventElapsedTime(&ms, e0, e1);
       if (rep == 1) tsum = ms;
     }
+    if (getenv("CORR2D_VERBOSE"))
+      fprintf(stderr, "corr2d tuner m=%d n1=%d n2=%d: bn=%d mirror=%d group=%d -> %.4f ms\n", m,
+              n1, n2e, c.bn, c.mirror, c.group, tsum);
     if (tsum < best) { best = tsum; bestc = c; }
   }
   cudaEventDestroy(e0);

@@ -73,8 +73,13 @@ def test_c2_homo_offset_baseline(ctx, prec):
     phi, psi = run(ctx, y, precision=prec)
     ophi, opsi, _, _ = oracle.corr2d(y, nthreads=oracle.max_threads())
     check(phi, psi, ophi, opsi, TOL[prec], f"c2 {prec}")
-    # exact symmetry from the mirrored tiles
+    # the tuner may pick full tiles: symmetric to rounding
+    assert rel(phi, phi.T) < 1e-6 and rel(psi, -psi.T) < 1e-6
+    # mirrored tiles: exactly symmetric / antisymmetric, zero diagonal of Psi
+    phi, psi = run(ctx, y, precision=prec, exact_symmetry=True)
+    check(phi, psi, ophi, opsi, TOL[prec], f"c2 {prec} exact symmetry")
     assert np.array_equal(phi, phi.T) and np.array_equal(psi, -psi.T)
+    assert np.all(np.diag(psi) == 0)
 
 
 def test_c3_hetero_with_preprocessing(ctx):
