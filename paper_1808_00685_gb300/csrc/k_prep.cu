@@ -2,26 +2,32 @@
 // DFT along the perturbation axis (Eqs. ref, dynspec, stdev, disFT; the half
 // spectrum of Sec. 4.2), producing the operand rows of the cross-spectrum.
 //
-// Tensor-core kernel (k_prep_tc): one CTA per 128 spectral variables, one
-// thread per variable.
-//   1. FP64 reference (perturbation mean or the caller's spectrum), FP64
-//      centering y - ref, FP64 sum of squares and maximum |y - ref|.
-//   2. The centred values, scaled by a power of two, are split into 16-bit
-//      planes (FP16 hi/lo, or one BF16 plane) and written to shared memory as
-//      the A operand (variables x perturbation steps, K-major, 128-byte
-//      swizzle), 64 steps at a time.
+// Tensor-core kernel (k_prep_tc): one CTA of 512 threads per 128 spectral
+// variables; four threads share a variable's perturbation steps.
+//   1. FP64 reference (perturbation mean or the caller's spectrum) from FP64
+//      partial sums; FP32 extremes of y give the range of y - ref.
+//   2. FP64 centering y - ref, rounded once to FP32, scaled by a power of two
+//      and split into 16-bit planes (FP16 hi/lo, or one BF16 plane), written
+//      to shared memory as the A operand (variables x steps, K-major,
+//      128-byte swizzle), 64 steps at a time; compensated FP32 sum of squares.
 //   3. tcgen05.mma contracts them with the twiddle matrix W (rows: cos and
 //      -sin of 2 pi ((omega j) mod m) / m, FP64-built, split likewise) into
 //      TMEM: D(nu, c) = sum_j y~(nu, j) W(c, j); with planes hi*hi + hi*lo +
 //      lo*hi.  The twiddle chunks arrive by bulk copy.
-//   4. Epilogue: each thread reads its row of D, rescales by a power of two,
-//      splits into planes and writes the operand rows (unweighted for stack 1,
-//      weight w = 1 / 2 for stack 2), the scale factor sigma^-alpha 2^-E and sigma.
+//   4. Epilogue (16 warps, four per TMEM lane quadrant): row maximum,
+//      power-of-two rescale, split into planes, operand rows (unweighted for
+//      stack 1, weight w = 1 / 2 for stack 2), scale sigma^-alpha 2^-E, sigma.
+// FP64 is kept to the mean and the centering subtraction: GB300's FP64 rate is
+// low, so the range comes from FP32 min/max and the sum of squares from FP32.
 #include <cmath>
 #include "internal.h"
 #include "ptx.cuh"
 
 namespace c2d {
+
+constexpr int PREP_THREADS = 512;
+constexpr int PREP_GROUPS = PREP_THREADS / PREP_ROWS;  // threads per variable
+constexpr int PREP_SCRATCH = PREP_GROUPS * PREP_ROWS * (8 + 4 + 4 + 4 + 4 + 4) + PREP_ROWS * 16;
 
 // 16 consecutive TMEM columns of this warp's lanes.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -45,30 +51,7 @@ __device__ __forceinline__ uint32_t pack_b2(__nv_bfloat16 a, __nv_bfloat16 b) {
   return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// Split 8 FP64 values into FP16 hi and lo 16-byte vectors.
-__device__ __forceinline__ void split8_f64(const double (&v)[8], uint4& hi, uint4& lo) {
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    __half h0 = __double2half(v[2 * e]), h1 = __double2half(v[2 * e + 1]);
-    __half l0 = __double2half(v[2 * e] - (double)__half2float(h0));
-    __half l1 = __double2half(v[2 * e + 1] - (double)__half2float(h1));
-    h[e] = pack_h2(h0, h1);
-    l[e] = pack_h2(l0, l1);
-  }
-  hi = make_uint4(h[0], h[1], h[2], h[3]);
-  lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
-__device__ __forceinline__ uint4 bf16x8_f64(const double (&v)[8]) {
-  uint32_t h[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e)
-    h[e] = pack_b2(__double2bfloat16(v[2 * e]), __double2bfloat16(v[2 * e + 1]));
-  return make_uint4(h[0], h[1], h[2], h[3]);
-}
-
-// FP32 -> FP16 hi/lo of 8 values (with per-value weight multiplier).
+// FP32 -> FP16 hi/lo of 8 values: hi = fp16(v), lo = fp16(v - hi).
 __device__ __forceinline__ void split8_f32(const float* v, uint4& hi, uint4& lo) {
   uint32_t h[4], l[4];
 #pragma unroll
@@ -91,16 +74,37 @@ __device__ __forceinline__ uint4 bf16x8_f32(const float* v) {
   return make_uint4(h[0], h[1], h[2], h[3]);
 }
 
-__device__ __forceinline__ uint32_t tmem_cols_for(int ncomp) {
+__host__ __device__ __forceinline__ uint32_t tmem_cols_for(int ncomp) {
   uint32_t c = 32;
   while ((int)c < ncomp) c <<= 1;
   return c;
 }
 
+// Write one operand chunk (g frequencies of Re and Im, already scaled) as
+// planes: SPLIT [Re_hi Im_hi Re_lo Im_lo] (16 each), BF16 [Re Im] (32 each).
 template <int P>
-__global__ void __launch_bounds__(128) k_prep_tc(const PrepJob* __restrict__ jobs,
-                                                 const PrepItem* __restrict__ items, int* err,
-                                                 unsigned long long limit_ns) {
+__device__ __forceinline__ void store_chunk(uint8_t* dst, const float* re, const float* im) {
+  uint4 outv[8];
+  if (P == 2) {
+    split8_f32(re, outv[0], outv[4]);
+    split8_f32(re + 8, outv[1], outv[5]);
+    split8_f32(im, outv[2], outv[6]);
+    split8_f32(im + 8, outv[3], outv[7]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) outv[q] = bf16x8_f32(re + 8 * q);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) outv[4 + q] = bf16x8_f32(im + 8 * q);
+  }
+  uint4* d = (uint4*)dst;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) d[q] = outv[q];
+}
+
+template <int P>
+__global__ void __launch_bounds__(PREP_THREADS) k_prep_tc(const PrepJob* __restrict__ jobs,
+                                                          const PrepItem* __restrict__ items,
+                                                          int* err, unsigned long long limit_ns) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const PrepItem item = items[blockIdx.x];
@@ -108,15 +112,24 @@ __global__ void __launch_bounds__(128) k_prep_tc(const PrepJob* __restrict__ job
   const int m = job.m, n = job.n, kp = job.kp;
   const int ncomp = 2 * kp;  // rows of W: cos block then -sin block
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int nu = item.tile * PREP_ROWS + t;
+  const int r = t % PREP_ROWS, g = t / PREP_ROWS;  // variable row, step group
+  const int nu = item.tile * PREP_ROWS + r;
   const bool valid = nu < n;
   const WaitCtl wc{err, limit_ns};
 
-  // shared memory: A planes (128 rows x 128 B each), W planes (ncomp rows x 128 B each)
+  // shared memory: A planes (128 rows x 128 B each), W planes (ncomp rows x
+  // 128 B each), reduction scratch, barriers
   uint8_t* sA = base;
   uint8_t* sW = base + P * PREP_ROWS * 128;
   const uint32_t wbytes = (uint32_t)ncomp * 128u;
-  uint64_t* bars = (uint64_t*)(sW + P * wbytes);
+  double* red_s = (double*)(sW + P * wbytes);              // [4][128] partial sums
+  float* red_mn = (float*)(red_s + PREP_GROUPS * PREP_ROWS);
+  float* red_mx = red_mn + PREP_GROUPS * PREP_ROWS;
+  float* red_ss = red_mx + PREP_GROUPS * PREP_ROWS;        // Kahan partials
+  float* red_max = red_ss + PREP_GROUPS * PREP_ROWS;       // epilogue row maxima
+  int* row_ey = (int*)(red_max + PREP_GROUPS * PREP_ROWS);      // 128 used, 512 reserved
+  double* row_ref = (double*)(row_ey + PREP_GROUPS * PREP_ROWS);
+  uint64_t* bars = (uint64_t*)(row_ref + PREP_ROWS);
   uint32_t* tmem_slot = (uint32_t*)(bars + 2);
   const uint32_t wbar = smem_u32(&bars[0]), mbar = smem_u32(&bars[1]);
   const uint32_t ncols = tmem_cols_for(ncomp);
@@ -130,48 +143,63 @@ __global__ void __launch_bounds__(128) k_prep_tc(const PrepJob* __restrict__ job
     tmem_alloc(smem_u32(tmem_slot), ncols);
     tmem_relinquish();
   }
-  // ---- 1. FP64 reference, sums of squares and range (Eqs. ref, dynspec, stdev)
+  // ---- 1. FP64 partial sums over steps j = g, g+4, ..., FP32 extremes
   const float* y = job.y;
   const long ld = job.ld;
-  // FP64 is kept to the two steps that need it (GB300's FP64 rate is low):
-  // the reference mean and the centering subtraction.  The range of y - ref
-  // comes from the FP32 extremes of y, the sum of squares from the centred
-  // FP32 values (compensated summation).
-  double ref = 0.0, amax = 0.0;
-  if (valid) {
-    float ymin = y[nu], ymax = ymin;
-    if (job.ref) {
-      for (int j = 1; j < m; ++j) {
-        const float v = y[(long)j * ld + nu];
-        ymin = fminf(ymin, v);
-        ymax = fmaxf(ymax, v);
+  {
+    double s = 0.0;
+    float mn = __int_as_float(0x7f800000), mx = -__int_as_float(0x7f800000);
+    if (valid) {
+      if (job.ref) {
+        for (int j = g; j < m; j += PREP_GROUPS) {
+          const float v = y[(long)j * ld + nu];
+          mn = fminf(mn, v);
+          mx = fmaxf(mx, v);
+        }
+      } else {
+        for (int j = g; j < m; j += PREP_GROUPS) {
+          const float v = y[(long)j * ld + nu];
+          s += (double)v;
+          mn = fminf(mn, v);
+          mx = fmaxf(mx, v);
+        }
       }
-      ref = (double)job.ref[nu];
-    } else {
-      double s = (double)ymin;
-      for (int j = 1; j < m; ++j) {
-        const float v = y[(long)j * ld + nu];
-        s += (double)v;
-        ymin = fminf(ymin, v);
-        ymax = fmaxf(ymax, v);
-      }
-      ref = s / (double)m;
     }
-    amax = fmax((double)ymax - ref, ref - (double)ymin);  // extremes of |y - ref|
+    red_s[g * PREP_ROWS + r] = s;
+    red_mn[g * PREP_ROWS + r] = mn;
+    red_mx[g * PREP_ROWS + r] = mx;
   }
-  float ss = 0.f, ss_c = 0.f;  // Kahan sum of (y - ref)^2
-  int ey = 0;
-  if (amax > 0.0) {
-    int e;
-    frexp(amax, &e);  // amax < 2^e
-    ey = 14 - e;      // scaled maximum in [2^13, 2^14)
-    if (ey > 126) ey = 126;  // keep 2^ey a normal FP32 number (data below ~1e-34)
-  }
-  const float fy = ldexpf(1.0f, ey);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if (g == 0) {
+    double ref = 0.0, amax = 0.0;
+    if (valid) {
+      float mn = red_mn[r], mx = red_mx[r];
+      double s = red_s[r];
+      for (int k = 1; k < PREP_GROUPS; ++k) {
+        s += red_s[k * PREP_ROWS + r];
+        mn = fminf(mn, red_mn[k * PREP_ROWS + r]);
+        mx = fmaxf(mx, red_mx[k * PREP_ROWS + r]);
+      }
+      ref = job.ref ? (double)job.ref[nu] : s / (double)m;
+      amax = fmax((double)mx - ref, ref - (double)mn);  // extremes of |y - ref|
+    }
+    int ey = 0;
+    if (amax > 0.0) {
+      int e;
+      frexp(amax, &e);  // amax < 2^e
+      ey = 14 - e;      // scaled maximum in [2^13, 2^14)
+      if (ey > 126) ey = 126;  // keep 2^ey a normal FP32 number (data below ~1e-34)
+    }
+    row_ref[r] = ref;
+    row_ey[r] = ey;
+  }
+  __syncthreads();
   const uint32_t tmem = *tmem_slot;
+  const double ref = row_ref[r];
+  const float fy = ldexpf(1.0f, row_ey[r]);
+  float ss = 0.f, ss_c = 0.f;  // Kahan sum of (y - ref)^2 over this thread's steps
   bool ok = true;
 
   // ---- 2./3. A chunks of 64 perturbation steps, MMA with the twiddle chunk
@@ -190,9 +218,10 @@ __global__ void __launch_bounds__(128) k_prep_tc(const PrepJob* __restrict__ job
         bulk_load(smem_u32(sW + p * wbytes), job.wtab + ((size_t)kc * P + p) * wbytes, wbytes,
                   wbar);
     }
-    // centred, scaled values of steps 64 kc .. 64 kc + 63 for this variable
-#pragma unroll 1
-    for (int jg = 0; jg < 8; ++jg) {
+    // this thread's two groups of 8 steps: jg = g and g + 4
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int jg = g + PREP_GROUPS * h;
       float v[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
@@ -205,7 +234,7 @@ __global__ void __launch_bounds__(128) k_prep_tc(const PrepJob* __restrict__ job
         ss = tsum;
         v[e] = d * fy;
       }
-      uint32_t off = sw128_off((uint32_t)t, (uint32_t)jg);
+      const uint32_t off = sw128_off((uint32_t)r, (uint32_t)jg);
       if (P == 2) {
         uint4 hi, lo;
         split8_f32(v, hi, lo);
@@ -231,9 +260,9 @@ __global__ void __launch_bounds__(128) k_prep_tc(const PrepJob* __restrict__ job
             const int pa = (cb == 2) ? 1 : 0, pw = (cb == 1) ? 1 : 0;
             const uint64_t ad = sw128_desc(a0 + pa * PREP_ROWS * 128 + ks * 32);
             const uint32_t acc = (kc > 0 || ks > 0 || cb > 0) ? 1u : 0u;
-            for (int h = 0; h < nhalf; ++h) {
-              const uint64_t bd = sw128_desc(w0 + pw * wbytes + h * 256 * 128 + ks * 32);
-              mma_f16(tmem + h * 256, ad, bd, h ? id1 : id0, acc);
+            for (int hh = 0; hh < nhalf; ++hh) {
+              const uint64_t bd = sw128_desc(w0 + pw * wbytes + hh * 256 * 128 + ks * 32);
+              mma_f16(tmem + hh * 256, ad, bd, hh ? id1 : id0, acc);
             }
           }
         }
@@ -242,18 +271,28 @@ __global__ void __launch_bounds__(128) k_prep_tc(const PrepJob* __restrict__ job
       }
     }
   }
+  red_ss[g * PREP_ROWS + r] = ss;
   ok = ok && mbar_wait(mbar, (jchunks - 1) & 1, wc);
   tc_fence_after();
 
-  // ---- 4. epilogue: row maximum, power-of-two rescale, planes, operand rows
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  // ---- 4. epilogue: 16 warps, warp w reads TMEM lane quadrant q = w % 4 and
+  // column part w / 4
+  const int q = warp & 3, part = warp >> 2;
+  const int lr = q * 32 + lane;                       // tile row (TMEM lane)
+  const int nu_e = item.tile * PREP_ROWS + lr;
+  const bool valid_e = nu_e < n;
+  const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
   float dmax = 0.f;
-  for (int c0 = 0; c0 < ncomp; c0 += 16) {
+  for (int b = part; b < ncomp / 16; b += 4) {
     float v[16];
-    tmem_ld16(trow + c0, v);
+    tmem_ld16(trow + b * 16, v);
 #pragma unroll
     for (int i = 0; i < 16; ++i) dmax = fmaxf(dmax, fabsf(v[i]));
   }
+  red_max[part * PREP_ROWS + lr] = dmax;
+  __syncthreads();
+  dmax = fmaxf(fmaxf(red_max[lr], red_max[PREP_ROWS + lr]),
+               fmaxf(red_max[2 * PREP_ROWS + lr], red_max[3 * PREP_ROWS + lr]));
   int eY = 0;
   if (dmax > 0.f) {
     int e;
@@ -261,11 +300,11 @@ __global__ void __launch_bounds__(128) k_prep_tc(const PrepJob* __restrict__ job
     eY = 14 - e;
   }
   const float fY = ldexpf(1.0f, eY);
-  const int g = (P == 2) ? 16 : 32;
-  const int nch = kp / g;
-  uint8_t* rowA = job.outA ? (uint8_t*)(job.outA + (size_t)(valid ? nu : 0) * job.rowlen) : nullptr;
-  uint8_t* rowB = job.outB ? (uint8_t*)(job.outB + (size_t)(valid ? nu : 0) * job.rowlen) : nullptr;
-  for (int c = 0; c < nch; ++c) {
+  const int gsz = (P == 2) ? 16 : 32;
+  const int nch = kp / gsz;
+  uint8_t* rowA = (job.outA && valid_e) ? (uint8_t*)(job.outA + (size_t)nu_e * job.rowlen) : nullptr;
+  uint8_t* rowB = (job.outB && valid_e) ? (uint8_t*)(job.outB + (size_t)nu_e * job.rowlen) : nullptr;
+  for (int c = part; c < nch; c += 4) {
     float re[32], im[32];
     if (P == 2) {
       float a[16], b[16];
@@ -280,58 +319,29 @@ __global__ void __launch_bounds__(128) k_prep_tc(const PrepJob* __restrict__ job
 #pragma unroll
       for (int i = 0; i < 32; ++i) { re[i] = a[i] * fY; im[i] = b[i] * fY; }
     }
-    if (!valid) continue;
-    uint4 outv[8];
-    // unweighted
-    if (rowA) {
-      if (P == 2) {
-        split8_f32(re, outv[0], outv[4]);
-        split8_f32(re + 8, outv[1], outv[5]);
-        split8_f32(im, outv[2], outv[6]);
-        split8_f32(im + 8, outv[3], outv[7]);
-      } else {
-        for (int q = 0; q < 4; ++q) outv[q] = bf16x8_f32(re + 8 * q);
-        for (int q = 0; q < 4; ++q) outv[4 + q] = bf16x8_f32(im + 8 * q);
-      }
-      uint4* dst = (uint4*)(rowA + (size_t)c * 128);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) dst[q] = outv[q];
-    }
+    if (rowA) store_chunk<P>(rowA + (size_t)c * 128, re, im);
     if (rowB) {
       // half-spectrum weight: 1 at omega = 0 (first element of chunk 0), else 2
-      const int gg = (P == 2) ? 16 : 32;
-      float rw[32], iw[32];
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
-        if (i < gg) {
-          float w = (c == 0 && i == 0) ? 1.f : 2.f;
-          rw[i] = re[i] * w;
-          iw[i] = im[i] * w;
-        }
+        const float wgt = (c == 0 && i == 0) ? 1.f : 2.f;
+        re[i] *= wgt;
+        im[i] *= wgt;
       }
-      if (P == 2) {
-        split8_f32(rw, outv[0], outv[4]);
-        split8_f32(rw + 8, outv[1], outv[5]);
-        split8_f32(iw, outv[2], outv[6]);
-        split8_f32(iw + 8, outv[3], outv[7]);
-      } else {
-        for (int q = 0; q < 4; ++q) outv[q] = bf16x8_f32(rw + 8 * q);
-        for (int q = 0; q < 4; ++q) outv[4 + q] = bf16x8_f32(iw + 8 * q);
-      }
-      uint4* dst = (uint4*)(rowB + (size_t)c * 128);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) dst[q] = outv[q];
+      store_chunk<P>(rowB + (size_t)c * 128, re, im);
     }
   }
-  if (valid) {
-    double sigma = sqrt(ss / (double)(m - 1));
+  if (part == 0 && valid_e) {
+    double s2sum = 0.0;
+    for (int k = 0; k < PREP_GROUPS; ++k) s2sum += (double)red_ss[k * PREP_ROWS + lr];
+    const double sigma = sqrt(s2sum / (double)(m - 1));
     double sc;
     if (job.alpha > 0.0)
       sc = (sigma == 0.0) ? 0.0 : pow(sigma, -job.alpha);
     else
       sc = 1.0;
-    job.scale[nu] = (float)ldexp(sc, -(ey + eY));
-    if (job.sigma_out) job.sigma_out[nu] = (float)sigma;
+    job.scale[nu_e] = (float)ldexp(sc, -(row_ey[lr] + eY));
+    if (job.sigma_out) job.sigma_out[nu_e] = (float)sigma;
   }
   if (t == 0 && !ok) {  // abort: let started copies and MMAs finish
     if (w_armed > 0) mbar_wait_drain(wbar, (w_armed - 1) & 1, limit_ns);
@@ -340,14 +350,13 @@ __global__ void __launch_bounds__(128) k_prep_tc(const PrepJob* __restrict__ job
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, ncols);
-  (void)lane;
 }
 
 static size_t prep_smem_bytes(int planes, int max_kp) {
-  size_t bytes = 1024 + (size_t)planes * PREP_ROWS * 128 + (size_t)planes * 2 * max_kp * 128 + 64;
+  size_t bytes = 1024 + (size_t)planes * PREP_ROWS * 128 + (size_t)planes * 2 * max_kp * 128 +
+                 PREP_SCRATCH + 64;
   // Keep (CTAs per SM) x (TMEM columns per CTA) <= 512 so allocation never waits.
-  uint32_t cols = 32;
-  while ((int)cols < 2 * max_kp) cols <<= 1;
+  const uint32_t cols = tmem_cols_for(2 * max_kp);
   const size_t sm_smem = 233472;  // shared memory per SM
   const size_t max_cta = 512 / cols;
   const size_t floor_bytes = sm_smem / (max_cta + 1) + 1024;
@@ -359,9 +368,9 @@ cudaError_t launch_prep_tc(const PrepJob* d_jobs, const PrepItem* d_items, int n
   if (nitems <= 0) return cudaSuccess;
   size_t smem = prep_smem_bytes(planes, max_kp);
   if (planes == 2)
-    k_prep_tc<2><<<nitems, 128, smem, s>>>(d_jobs, d_items, err, limit_ns);
+    k_prep_tc<2><<<nitems, PREP_THREADS, smem, s>>>(d_jobs, d_items, err, limit_ns);
   else
-    k_prep_tc<1><<<nitems, 128, smem, s>>>(d_jobs, d_items, err, limit_ns);
+    k_prep_tc<1><<<nitems, PREP_THREADS, smem, s>>>(d_jobs, d_items, err, limit_ns);
   return cudaGetLastError();
 }
 
@@ -414,13 +423,13 @@ __global__ void __launch_bounds__(256) k_prep_simt(SimtPrepJob job) {
   }
   for (int w = warp; w < job.kp1; w += 8) {
     float re = 0.f, im = 0.f;
-    int r = 0;  // (w * j) mod m, advanced incrementally
+    int rr = 0;  // (w * j) mod m, advanced incrementally
     for (int j = 0; j < m; ++j) {
       float d = yt[(size_t)j * 32 + lane];
-      re = fmaf(d, tw[2 * r], re);
-      im = fmaf(-d, tw[2 * r + 1], im);
-      r += w;
-      if (r >= m) r -= m;
+      re = fmaf(d, tw[2 * rr], re);
+      im = fmaf(-d, tw[2 * rr + 1], im);
+      rr += w;
+      if (rr >= m) rr -= m;
     }
     if (valid) {
       if (job.yr) {

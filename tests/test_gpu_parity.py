@@ -188,6 +188,25 @@ def test_mirror_and_full_tiles_agree(ctx):
     check(*b, ophi, opsi, 1e-5, "no mirror")
 
 
+def test_repeated_calls_reuse_descriptors_correctly(ctx):
+    """Identical calls launch from cached device descriptors; another shape in
+    between must not leave a stale cache, and new input data must be used."""
+    import paper_1808_00685_gb300 as pkg
+    ya = workloads.random_stack(20, 300, seed=31)
+    yb = workloads.random_stack(33, 170, seed=32)
+    da, db = dev(ya), dev(yb)
+    oa, ob = pkg.Context.alloc_out(300, 300, da.device), pkg.Context.alloc_out(170, 170, db.device)
+    for step in range(3):
+        for y, d, o in ((ya, da, oa), (yb, db, ob)):
+            n = y.shape[1]
+            phi, psi = ctx.compute(d, out=o[:2])
+            ctx.synchronize()
+            ophi, opsi, _, _ = oracle.corr2d(y)
+            check(host(phi)[:, :n], host(psi)[:, :n], ophi, opsi, 1e-5, f"step {step} n={n}")
+        ya *= np.float32(1.5)  # new data in the same buffer
+        da.copy_(torch.from_numpy(ya))
+
+
 def test_self_hetero_matches_homo(ctx):
     y = workloads.random_stack(30, 260, seed=8)
     a = run(ctx, y, precision="split", no_mirror=True)
