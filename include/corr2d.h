@@ -80,6 +80,12 @@ typedef enum {
  * not bit-for-bit symmetric.  This flag keeps the mirrored tiles, so Phi is
  * exactly symmetric and Psi exactly antisymmetric with a zero diagonal. */
 #define CORR2D_FLAG_EXACT_SYMMETRY 2u
+/* Hilbert-transform approach instead of the Fourier-transform one (Sec. 2,
+ * Eqs. disHTsyn, disHT, HilbNoda, disHTasyn):
+ *   Phi = Norm sum_j y~1(t_j) y~2(t_j),  Psi = Norm sum_j y~1(t_j) z~2(t_j),
+ *   z~2 = N y~2 with the Hilbert-Noda matrix N_jk = 1/(pi (k - j)), N_jj = 0,
+ * default Norm 1/(m - 1).  Tensor-core precisions only, m <= 256. */
+#define CORR2D_FLAG_HILBERT 4u
 
 typedef struct {
   int ref_mode;       /* corr2d_ref_mode */

@@ -31,6 +31,7 @@ PREC_FP32, PREC_SPLIT, PREC_BF16 = 0, 1, 2
 REF_MEAN, REF_USER = 0, 1
 FLAG_NO_MIRROR = 1
 FLAG_EXACT_SYMMETRY = 2
+FLAG_HILBERT = 4
 _PREC_BY_NAME = {"fp32": PREC_FP32, "split": PREC_SPLIT, "bf16": PREC_BF16}
 
 EXPORTED_SYMBOLS = (
@@ -197,7 +198,7 @@ def _ptr(t):
 
 
 def make_params(precision="split", alpha=0.0, norm=0.0, ref1=None, ref2=None,
-                no_mirror=False, exact_symmetry=False) -> corr2d_params:
+                no_mirror=False, exact_symmetry=False, hilbert=False) -> corr2d_params:
     p = corr2d_params_default()
     p.precision = _PREC_BY_NAME[precision] if isinstance(precision, str) else int(precision)
     p.alpha = float(alpha)
@@ -206,7 +207,8 @@ def make_params(precision="split", alpha=0.0, norm=0.0, ref1=None, ref2=None,
         p.ref_mode = REF_USER
         p.ref1 = _ptr(ref1)
         p.ref2 = _ptr(ref2)
-    p.flags = (FLAG_NO_MIRROR if no_mirror else 0) | (FLAG_EXACT_SYMMETRY if exact_symmetry else 0)
+    p.flags = ((FLAG_NO_MIRROR if no_mirror else 0) | (FLAG_EXACT_SYMMETRY if exact_symmetry else 0)
+               | (FLAG_HILBERT if hilbert else 0))
     return p
 
 
@@ -258,7 +260,8 @@ class Context:
         return phi, psi, ldo
 
     def compute(self, y1, y2=None, precision="split", alpha=0.0, norm=0.0, ref1=None, ref2=None,
-                no_mirror=False, out=None, want_sigma=False, exact_symmetry=False):
+                no_mirror=False, out=None, want_sigma=False, exact_symmetry=False,
+                hilbert=False):
         """Phi, Psi (n1 x n2 views) of the m x n1 stack y1 (and y2, or homo)."""
         import torch
         assert y1.is_cuda and y1.dtype == torch.float32 and y1.dim() == 2
@@ -274,7 +277,8 @@ class Context:
         s1 = torch.empty(n1, dtype=torch.float32, device=y1.device) if want_sigma else None
         s2 = (torch.empty(n2, dtype=torch.float32, device=y1.device)
               if (want_sigma and y2 is not None) else None)
-        params = make_params(precision, alpha, norm, ref1, ref2, no_mirror, exact_symmetry)
+        params = make_params(precision, alpha, norm, ref1, ref2, no_mirror, exact_symmetry,
+                             hilbert)
         corr2d_compute(self.handle, m, n1, _ptr(y1), y1.stride(0), n2, _ptr(y2),
                        y2.stride(0) if y2 is not None else 0, params, _ptr(phi), _ptr(psi), ldo,
                        _ptr(s1), _ptr(s2))
@@ -292,7 +296,8 @@ class Context:
                           _ptr(ref), _ptr(dyn))
         return out, dyn
 
-    def batch(self, problems, precision="split", alpha=0.0, norm=0.0, no_mirror=False):
+    def batch(self, problems, precision="split", alpha=0.0, norm=0.0, no_mirror=False,
+              hilbert=False):
         """problems: list of (y1, y2 or None, phi, psi) torch tensors (phi/psi n1 x ldo)."""
         ps = []
         for y1, y2, phi, psi in problems:
@@ -300,7 +305,8 @@ class Context:
             n2 = n1 if y2 is None else y2.shape[1]
             ps.append(corr2d_problem(m, n1, n2, _ptr(y1), _ptr(y2), _ptr(phi), _ptr(psi),
                                      phi.stride(0)))
-        corr2d_batch(self.handle, ps, make_params(precision, alpha, norm, None, None, no_mirror))
+        corr2d_batch(self.handle, ps, make_params(precision, alpha, norm, None, None, no_mirror,
+                                                  hilbert=hilbert))
 
     def compute_host(self, y1, y2=None, precision="split", alpha=0.0, norm=0.0, out=None):
         """Host (CPU) tensors in and out; copies overlap the kernels inside the library."""

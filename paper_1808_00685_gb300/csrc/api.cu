@@ -78,7 +78,7 @@ struct corr2d_ctx {
   DevBuf ops;       // operand rows / frequency planes of corr2d_compute
   DevBuf desc;      // uploaded descriptors of corr2d_compute
   std::vector<uint8_t> desc_host;  // last uploaded descriptor bytes
-  std::map<std::pair<int, int>, DevBuf> twiddles;  // (m, planes) -> table
+  std::map<std::pair<int, int>, DevBuf> twiddles;  // (m, planes + 4 kind) -> table
   std::map<int, DevBuf> simt_tw;                    // m -> FP32 cos/sin table
   std::map<std::tuple<int, int, int, int, int>, TileChoice> tuned;  // shape -> choice
   BatchCache batch;
@@ -180,13 +180,14 @@ corr2d_status check_params(corr2d_ctx* ctx, const corr2d_params* p, bool homo) {
 }
 
 // Twiddle table of the tensor-core DFT for (m, planes), built once per context.
-corr2d_status get_twiddles(corr2d_ctx* ctx, int m, int planes, const uint8_t** out) {
-  auto key = std::make_pair(m, planes);
+corr2d_status get_twiddles(corr2d_ctx* ctx, int m, int planes, const uint8_t** out,
+                           int kind = XF_DFT) {
+  auto key = std::make_pair(m, planes + 4 * kind);
   auto it = ctx->twiddles.find(key);
   if (it == ctx->twiddles.end()) {
-    size_t bytes = make_twiddles(m, planes, nullptr);
+    size_t bytes = make_transform(m, planes, kind, nullptr);
     std::vector<uint8_t> host(bytes);
-    make_twiddles(m, planes, host.data());
+    make_transform(m, planes, kind, host.data());
     DevBuf b;
     corr2d_status st = ensure(ctx, b, bytes);
     if (st != CORR2D_OK) return st;
@@ -321,11 +322,19 @@ struct TcPlan {
   size_t bytesA, bytesB, off_s1, off_s2, total;
 };
 
-TcPlan plan_tc(int m, int n1, int n2, bool homo, int precision) {
+// Normalisation: the caller's, else 1/(pi (m-1)) for the FT approach
+// (Eq. disint2d) or 1/(m-1) for the Hilbert approach (Eqs. disHTsyn/disHTasyn).
+double default_norm(const corr2d_params& p, int m) {
+  if (p.norm > 0.0) return p.norm;
+  if (p.flags & CORR2D_FLAG_HILBERT) return 1.0 / (double)(m - 1);
+  return 1.0 / (kPi * (double)(m - 1));
+}
+
+TcPlan plan_tc(int m, int n1, int n2, bool homo, int precision, bool hilbert = false) {
   TcPlan p;
   p.planes = precision == CORR2D_PREC_SPLIT ? 2 : 1;
-  p.kp = freq_padded(m, p.planes);
-  p.nch = chunks_for(m, p.planes);
+  p.kp = comps_padded(m, p.planes, hilbert);
+  p.nch = p.kp / freq_group(p.planes);
   p.rowlen = p.nch * CHUNK_ELEMS;
   p.bytesA = align_up((size_t)n1 * p.rowlen * 2, 1024);
   p.bytesB = align_up((size_t)n2 * p.rowlen * 2, 1024);
@@ -346,12 +355,15 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
                          bool skip_prep, DevBuf& opsbuf, DevBuf& descbuf,
                          std::vector<uint8_t>& desc_last, LaunchPlan* cache = nullptr) {
   const bool homo = (y2 == nullptr);
-  TcPlan pl = plan_tc(m, n1, n2, homo, p.precision);
+  const bool hilbert = (p.flags & CORR2D_FLAG_HILBERT) != 0;
+  TcPlan pl = plan_tc(m, n1, n2, homo, p.precision, hilbert);
   corr2d_status st = ensure(ctx, opsbuf, pl.total);
   if (st != CORR2D_OK) return st;
-  const uint8_t* wtab = nullptr;
-  st = get_twiddles(ctx, m, pl.planes, &wtab);
+  const uint8_t* wtab = nullptr;    // stack 1 (and homo DFT: both)
+  const uint8_t* wtab_b = nullptr;  // stack 2 of the Hilbert variant
+  st = get_twiddles(ctx, m, pl.planes, &wtab, hilbert ? XF_HT_A : XF_DFT);
   if (st != CORR2D_OK) return st;
+  if (hilbert && (st = get_twiddles(ctx, m, pl.planes, &wtab_b, XF_HT_B)) != CORR2D_OK) return st;
   auto launch = [&](const uint8_t* d, const LaunchPlan& lp) -> corr2d_status {
     if (ctx->profiling) cudaEventRecord(ctx->ev[0], ctx->stream);
     if (!lp.skip_prep)
@@ -397,22 +409,26 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   std::vector<PrepJob> jobs;
   std::vector<PrepItem> pitems;
   auto mkjob = [&](const float* y, long ld, int n, const float* ref, uint16_t* a, uint16_t* b,
-                   float* sc, float* sig) {
+                   float* sc, float* sig, const uint8_t* table) {
     PrepJob j{};
     j.y = y; j.ref = ref; j.outA = a; j.outB = b; j.scale = sc; j.sigma_out = sig;
-    j.wtab = wtab; j.ld = ld; j.m = m; j.n = n; j.kp = pl.kp; j.jchunks = (m + 63) / 64;
-    j.rowlen = pl.rowlen; j.alpha = p.alpha;
+    j.wtab = table; j.ld = ld; j.m = m; j.n = n; j.kp = pl.kp; j.jchunks = (m + 63) / 64;
+    j.rowlen = pl.rowlen; j.alpha = p.alpha; j.plain_weights = hilbert ? 1 : 0;
     int id = (int)jobs.size();
     jobs.push_back(j);
     for (int t = 0; t < (n + PREP_ROWS - 1) / PREP_ROWS; ++t) pitems.push_back(PrepItem{id, t});
   };
   const float* r1 = p.ref_mode == CORR2D_REF_USER ? p.ref1 : nullptr;
   const float* r2 = p.ref_mode == CORR2D_REF_USER ? (homo ? p.ref1 : p.ref2) : nullptr;
-  if (homo) {
-    mkjob(y1, ld1, n1, r1, opA, opB, s1, sig1);
+  if (homo && !hilbert) {
+    mkjob(y1, ld1, n1, r1, opA, opB, s1, sig1, wtab);
+  } else if (homo) {
+    // the two operands of the Hilbert variant use different matrices
+    mkjob(y1, ld1, n1, r1, opA, nullptr, s1, sig1, wtab);
+    mkjob(y1, ld1, n1, r1, nullptr, opB, s1, nullptr, wtab_b);
   } else {
-    mkjob(y1, ld1, n1, r1, opA, nullptr, s1, sig1);
-    mkjob(y2, ld2, n2, r2, nullptr, opB, s2, sig2);
+    mkjob(y1, ld1, n1, r1, opA, nullptr, s1, sig1, wtab);
+    mkjob(y2, ld2, n2, r2, nullptr, opB, s2, sig2, hilbert ? wtab_b : wtab);
   }
   XProblem xp;
   memset(&xp, 0, sizeof xp);
@@ -422,7 +438,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   if ((st = encode_output(ctx, &xp.tmPsi, psi, out_rows, n2, ldo)) != CORR2D_OK) return st;
   xp.s1 = s1;
   xp.s2 = s2;
-  xp.norm = (float)(p.norm > 0.0 ? p.norm : 1.0 / (kPi * (double)(m - 1)));
+  xp.norm = (float)default_norm(p, m);
   xp.n1 = n1;
   xp.n2 = n2;
   xp.nchunks = pl.nch;
@@ -512,7 +528,16 @@ corr2d_status enqueue_simt(corr2d_ctx* ctx, int m, int n1, const float* y1, int 
 // plane as 128-byte-swizzled rows, the layout tcgen05 reads from shared memory.
 // ---------------------------------------------------------------------------
 size_t c2d::make_twiddles(int m, int planes, uint8_t* out) {
-  const int kp = freq_padded(m, planes);
+  return make_transform(m, planes, XF_DFT, out);
+}
+
+// Hilbert variant (Eqs. disHT, HilbNoda): row c of the "Im" block of stack 2
+// holds -N_cj = -1/(pi (j - c)) for j != c and 0 on the diagonal, so that the
+// component c of the operand row is -(N y~)(t_c); the "Re" block is the
+// identity.  Stack 1's "Im" block is zero.
+size_t c2d::make_transform(int m, int planes, int kind, uint8_t* out) {
+  const bool hilbert = kind != XF_DFT;
+  const int kp = comps_padded(m, planes, hilbert);
   const int K = freq_count(m) - 1;
   const int ncomp = 2 * kp;
   const int jchunks = (m + 63) / 64;
@@ -522,14 +547,21 @@ size_t c2d::make_twiddles(int m, int planes, uint8_t* out) {
   memset(out, 0, total);
   for (int kc = 0; kc < jchunks; ++kc)
     for (int c = 0; c < ncomp; ++c) {
-      const int w = c < kp ? c : c - kp;
-      if (w > K) continue;
+      const int w = c < kp ? c : c - kp;  // frequency (DFT) or perturbation step (Hilbert)
+      if (hilbert ? (w >= m || (c >= kp && kind == XF_HT_A)) : (w > K)) continue;
       for (int jj = 0; jj < 64; ++jj) {
         const int j = kc * 64 + jj;
         if (j >= m) break;
-        const long r = ((long)w * (long)j) % (long)m;
-        const double th = 2.0 * kPi * (double)r / (double)m;
-        const double val = c < kp ? std::cos(th) : -std::sin(th);
+        double val;
+        if (hilbert) {
+          if (c < kp) val = (j == w) ? 1.0 : 0.0;
+          else val = (j == w) ? 0.0 : -1.0 / (kPi * (double)(j - w));
+        } else {
+          const long r = ((long)w * (long)j) % (long)m;
+          const double th = 2.0 * kPi * (double)r / (double)m;
+          val = c < kp ? std::cos(th) : -std::sin(th);
+        }
+        if (val == 0.0) continue;
         const size_t off = (size_t)c * 128 + ((((size_t)jj / 8) ^ ((size_t)c & 7)) << 4) +
                            (size_t)(jj % 8) * 2;
         if (planes == 2) {
@@ -719,6 +751,12 @@ static corr2d_status validate_compute(corr2d_ctx* ctx, int m, int n1, const floa
   const bool tc = p.precision != CORR2D_PREC_FP32;
   if (!tc && m > MAX_M_FP32)
     return fail(ctx, CORR2D_EUNSUPPORTED, "the FP32 path supports m <= %d", MAX_M_FP32);
+  if (p.flags & CORR2D_FLAG_HILBERT) {
+    if (!tc)
+      return fail(ctx, CORR2D_EUNSUPPORTED, "the Hilbert-transform variant runs the tensor-core precisions");
+    if (m > MAX_M_HT)
+      return fail(ctx, CORR2D_EUNSUPPORTED, "the Hilbert-transform variant supports m <= %d", MAX_M_HT);
+  }
   if (tc) {
     if (m > MAX_M_TC)
       return fail(ctx, CORR2D_EUNSUPPORTED, "tensor-core precisions support m <= %d (use FP32)", MAX_M_TC);
@@ -744,8 +782,9 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
   const bool homo = (y2 == nullptr);
   const int n2e = homo ? n1 : n2;
   auto key = std::make_tuple(m, n1, n2e, homo ? 1 : 0,
-                             p.precision * 4 + (int)(p.flags & (CORR2D_FLAG_NO_MIRROR |
-                                                                CORR2D_FLAG_EXACT_SYMMETRY)));
+                             p.precision * 8 + (int)(p.flags & (CORR2D_FLAG_NO_MIRROR |
+                                                                CORR2D_FLAG_EXACT_SYMMETRY |
+                                                                CORR2D_FLAG_HILBERT)));
   auto it = ctx->tuned.find(key);
   if (it != ctx->tuned.end()) { *out = it->second; return CORR2D_OK; }
   std::vector<TileChoice> cands;
@@ -859,10 +898,13 @@ corr2d_status corr2d_compute_host(corr2d_ctx* ctx, int m, int n1, const float* y
   int slab_tiles = (int)std::max<long>(1, std::min<long>(nt1, (256l << 20) / ((long)TILE_M * ld_dev * 8)));
   const size_t slab_bytes = align_up((size_t)slab_tiles * TILE_M * ld_dev * 4, 1024);
   if ((st = ensure(ctx, ctx->host_out, 4 * slab_bytes)) != CORR2D_OK) return st;
-  cudaStream_t copy;
+  // Phi and Psi slabs go back on two streams (two copy engines)
+  cudaStream_t copy, copy2;
   CUDA_TRY(ctx, cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking));
-  cudaEvent_t done[2], freed[2];
+  CUDA_TRY(ctx, cudaStreamCreateWithFlags(&copy2, cudaStreamNonBlocking));
+  cudaEvent_t done[2], freed[2], freed2[2];
   for (int i = 0; i < 2; ++i) {
+    cudaEventCreateWithFlags(&freed2[i], cudaEventDisableTiming);
     cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
     cudaEventCreateWithFlags(&freed[i], cudaEventDisableTiming);
   }
@@ -877,32 +919,40 @@ corr2d_status corr2d_compute_host(corr2d_ctx* ctx, int m, int n1, const float* y
     const int sb = k & 1;
     float* sphi = (float*)((uint8_t*)ctx->host_out.p + (2 * sb) * slab_bytes);
     float* spsi = (float*)((uint8_t*)ctx->host_out.p + (2 * sb + 1) * slab_bytes);
-    if (k >= 2) cudaStreamWaitEvent(ctx->stream, freed[sb], 0);
+    if (k >= 2) {  // both copies out of this slab buffer have finished
+      cudaStreamWaitEvent(ctx->stream, freed[sb], 0);
+      cudaStreamWaitEvent(ctx->stream, freed2[sb], 0);
+    }
     const int rows = std::min(n1, t1 * TILE_M) - t0 * TILE_M;
     result = enqueue_tc(ctx, m, n1, d1, n1, n2, d2, n2, p, sphi, spsi, ld_dev, rows, nullptr,
                         nullptr, tc, t0, t1, t0, k > 0, ctx->ops, slab_desc[sb], slab_last[sb]);
     if (result != CORR2D_OK) break;
     cudaEventRecord(done[sb], ctx->stream);
     cudaStreamWaitEvent(copy, done[sb], 0);
+    cudaStreamWaitEvent(copy2, done[sb], 0);
     cudaError_t e1 = cudaMemcpy2DAsync(phi + (size_t)t0 * TILE_M * ldo, ldo * 4, sphi, ld_dev * 4,
                                        (size_t)n2 * 4, rows, cudaMemcpyDeviceToHost, copy);
     cudaError_t e2 = cudaMemcpy2DAsync(psi + (size_t)t0 * TILE_M * ldo, ldo * 4, spsi, ld_dev * 4,
-                                       (size_t)n2 * 4, rows, cudaMemcpyDeviceToHost, copy);
+                                       (size_t)n2 * 4, rows, cudaMemcpyDeviceToHost, copy2);
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
       result = fail(ctx, CORR2D_ECUDA, "device-to-host copy failed: %s",
                     cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
       break;
     }
     cudaEventRecord(freed[sb], copy);
+    cudaEventRecord(freed2[sb], copy2);
   }
   cudaStreamSynchronize(copy);
+  cudaStreamSynchronize(copy2);
   cudaStreamSynchronize(ctx->stream);
   for (int i = 0; i < 2; ++i) {
     cudaEventDestroy(done[i]);
     cudaEventDestroy(freed[i]);
+    cudaEventDestroy(freed2[i]);
     release(slab_desc[i]);
   }
   cudaStreamDestroy(copy);
+  cudaStreamDestroy(copy2);
   (void)last;
   if (result != CORR2D_OK) return result;
   return corr2d_synchronize(ctx);
@@ -950,6 +1000,7 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
     return CORR2D_OK;
   }
   const int planes = p.precision == CORR2D_PREC_SPLIT ? 2 : 1;
+  const bool hilbert = (p.flags & CORR2D_FLAG_HILBERT) != 0;
   // workspace layout
   std::vector<size_t> offA(count), offB(count), offS1(count), offS2(count);
   size_t total = 0;
@@ -958,7 +1009,7 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
     const corr2d_problem& q = hp[i];
     const bool homo = q.y2 == nullptr;
     const int n2 = homo ? q.n1 : q.n2;
-    TcPlan pl = plan_tc(q.m, q.n1, n2, homo, p.precision);
+    TcPlan pl = plan_tc(q.m, q.n1, n2, homo, p.precision, hilbert);
     max_kp = std::max(max_kp, pl.kp);
     offA[i] = total; total += pl.bytesA;
     offB[i] = total; total += pl.bytesB;
@@ -977,28 +1028,34 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
       const corr2d_problem& q = hp[i];
       const bool homo = q.y2 == nullptr;
       const int n2 = homo ? q.n1 : q.n2;
-      TcPlan pl = plan_tc(q.m, q.n1, n2, homo, p.precision);
+      TcPlan pl = plan_tc(q.m, q.n1, n2, homo, p.precision, hilbert);
       const uint8_t* wtab = nullptr;
-      corr2d_status s2 = get_twiddles(ctx, q.m, planes, &wtab);
+      const uint8_t* wtab_b = nullptr;
+      corr2d_status s2 = get_twiddles(ctx, q.m, planes, &wtab, hilbert ? XF_HT_A : XF_DFT);
       if (s2 != CORR2D_OK) return s2;
+      if (hilbert && (s2 = get_twiddles(ctx, q.m, planes, &wtab_b, XF_HT_B)) != CORR2D_OK) return s2;
       uint16_t* opA = (uint16_t*)(ops + offA[i]);
       uint16_t* opB = (uint16_t*)(ops + offB[i]);
       float* sc1 = (float*)(ops + offS1[i]);
       float* sc2 = homo ? sc1 : (float*)(ops + offS2[i]);
-      auto mkjob = [&](const float* y, int n, uint16_t* a, uint16_t* b, float* sc) {
+      auto mkjob = [&](const float* y, int n, uint16_t* a, uint16_t* b, float* sc,
+                       const uint8_t* table) {
         PrepJob j{};
         j.y = y; j.ref = nullptr; j.outA = a; j.outB = b; j.scale = sc; j.sigma_out = nullptr;
-        j.wtab = wtab; j.ld = n; j.m = q.m; j.n = n; j.kp = pl.kp; j.jchunks = (q.m + 63) / 64;
-        j.rowlen = pl.rowlen; j.alpha = p.alpha;
+        j.wtab = table; j.ld = n; j.m = q.m; j.n = n; j.kp = pl.kp; j.jchunks = (q.m + 63) / 64;
+        j.rowlen = pl.rowlen; j.alpha = p.alpha; j.plain_weights = hilbert ? 1 : 0;
         int id = (int)jobs.size();
         jobs.push_back(j);
         for (int t = 0; t < (n + PREP_ROWS - 1) / PREP_ROWS; ++t) pitems.push_back(PrepItem{id, t});
       };
-      if (homo) {
-        mkjob(q.y1, q.n1, opA, opB, sc1);
+      if (homo && !hilbert) {
+        mkjob(q.y1, q.n1, opA, opB, sc1, wtab);
+      } else if (homo) {
+        mkjob(q.y1, q.n1, opA, nullptr, sc1, wtab);
+        mkjob(q.y1, q.n1, nullptr, opB, sc1, wtab_b);
       } else {
-        mkjob(q.y1, q.n1, opA, nullptr, sc1);
-        mkjob(q.y2, n2, nullptr, opB, sc2);
+        mkjob(q.y1, q.n1, opA, nullptr, sc1, wtab);
+        mkjob(q.y2, n2, nullptr, opB, sc2, hilbert ? wtab_b : wtab);
       }
       const int bn = (std::max(q.n1, n2) <= bn_threshold) ? 64 : 128;
       XProblem xp;
@@ -1008,7 +1065,7 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
       if ((s2 = encode_output(ctx, &xp.tmPhi, q.phi, q.n1, n2, q.ldo)) != CORR2D_OK) return s2;
       if ((s2 = encode_output(ctx, &xp.tmPsi, q.psi, q.n1, n2, q.ldo)) != CORR2D_OK) return s2;
       xp.s1 = sc1; xp.s2 = sc2;
-      xp.norm = (float)(p.norm > 0.0 ? p.norm : 1.0 / (kPi * (double)(q.m - 1)));
+      xp.norm = (float)default_norm(p, q.m);
       xp.n1 = q.n1; xp.n2 = n2; xp.nchunks = pl.nch;
       xp.mirror = (homo && bn == 128 && !(p.flags & CORR2D_FLAG_NO_MIRROR)) ? 1 : 0;
       xp.bn = bn;

@@ -37,6 +37,24 @@ inline int freq_padded(int m, int planes) {
 }
 inline int chunks_for(int m, int planes) { return freq_padded(m, planes) / freq_group(planes); }
 
+// Contraction applied along the perturbation axis by the prep kernel.  The
+// operand row of a variable holds two blocks of components ("Re", "Im"):
+//   XF_DFT      Re = cos, Im = -sin of 2 pi omega j / m, omega = 0..K  (Eq. disFT)
+//   XF_HT_A     Re = y~ (identity), Im = 0                     (stack 1 of the
+//   XF_HT_B     Re = y~ (identity), Im = -N y~ (Eq. HilbNoda)   Hilbert variant)
+// With these rows the cross-spectrum kernel's Phi = <Re1,Re2> + <Im1,Im2> and
+// Psi = <Im1,Re2> - <Re1,Im2> become Eqs. disHTsyn and disHTasyn.
+enum TransformKind : int { XF_DFT = 0, XF_HT_A = 1, XF_HT_B = 2 };
+constexpr int MAX_M_HT = 256;     // the Hilbert variant keeps 2 m components in TMEM
+inline int comps_padded(int m, int planes, bool hilbert) {
+  const int g = freq_group(planes);
+  return hilbert ? (m + g - 1) / g * g : freq_padded(m, planes);
+}
+// Table of the contraction matrix of `kind` for m steps, pre-swizzled for
+// tcgen05 (rows = components, 64 steps per 128-byte row, one block per
+// 64-step chunk and plane).  Returns its size; fills `out` when non-null.
+size_t make_transform(int m, int planes, int kind, uint8_t* out);
+
 // One stack's DFT job (tensor-core prep kernel).
 struct PrepJob {
   const float* y;          // m x n, leading dimension ld
@@ -51,7 +69,8 @@ struct PrepJob {
   int kp;                  // K'p
   int jchunks;             // ceil(m / 64)
   int rowlen;              // operand row length in elements
-  int pad_;
+  int plain_weights;       // 1: outB gets weight 1 everywhere (Hilbert variant);
+                           // 0: the half-spectrum weights 1 (omega = 0) / 2
   double alpha;
 };
 

@@ -321,10 +321,11 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep_tc(const PrepJob* __restr
     }
     if (rowA) store_chunk<P>(rowA + (size_t)c * 128, re, im);
     if (rowB) {
-      // half-spectrum weight: 1 at omega = 0 (first element of chunk 0), else 2
+      // half-spectrum weight: 1 at omega = 0 (first element of chunk 0), else 2;
+      // 1 everywhere for the Hilbert variant
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
-        const float wgt = (c == 0 && i == 0) ? 1.f : 2.f;
+        const float wgt = (job.plain_weights || (c == 0 && i == 0)) ? 1.f : 2.f;
         re[i] *= wgt;
         im[i] *= wgt;
       }
