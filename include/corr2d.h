@@ -142,6 +142,24 @@ corr2d_status corr2d_preprocess(corr2d_ctx* ctx, int m, int n_raw, const double*
                                 float* dyn_out);
 
 /*
+ * Interpolation along the perturbation axis onto N equidistant perturbation
+ * values (Sec. 4.2: the FT approach needs evenly spaced perturbation values;
+ * the new values are seq(min(Time), max(Time), length.out = N) and every
+ * spectral variable is evaluated there through an interpolating function of
+ * its values over Time -- here the linear one, approxfun).
+ *   m      perturbation steps of y, >= 2
+ *   n      spectral variables, >= 1
+ *   time   device, m FP64 perturbation values, strictly increasing and finite
+ *          (checked by a kernel; corr2d_synchronize() reports EINVAL)
+ *   y, ld  device, m x n FP32 stack, leading dimension ld >= n
+ *   N      new number of perturbation steps, >= 2 (powers of two suit the FFT
+ *          of the paper; any N works here)
+ *   y_out  device, N x n FP32, leading dimension n
+ */
+corr2d_status corr2d_preprocess_perturbation(corr2d_ctx* ctx, int m, int n, const double* time,
+                                             const float* y, int ld, int N, float* y_out);
+
+/*
  * Synchronous and asynchronous correlation spectra of one problem.
  *   m          perturbation steps shared by both stacks, >= 2 (the
  *              normalisation divides by m - 1); tensor-core precisions

@@ -81,6 +81,9 @@ def _configure(lib):
         ctypes.c_int, ctypes.c_int, _dp, _fp, ctypes.c_long, ctypes.c_int, _dp, _fp, _dp]
     lib.oracle_hilbert_noda.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp,
                                         _dp, _dp]
+    lib.oracle_interp_perturbation.restype = ctypes.c_int
+    lib.oracle_interp_perturbation.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _fp,
+                                               ctypes.c_long, ctypes.c_int, _dp]
     lib.oracle_max_threads.restype = ctypes.c_int
     return lib
 
@@ -282,6 +285,19 @@ def interp_linear(x_raw: np.ndarray, y_raw: np.ndarray, n_out: int, ref=None):
     if rc != 0:
         raise ValueError("oracle_interp_linear rejected its arguments")
     return out, dyn
+
+
+def interp_perturbation(time: np.ndarray, y: np.ndarray, N: int) -> np.ndarray:
+    """Linear resampling along the perturbation axis onto N equidistant values
+    (Sec. 4.2 interpolation snippet, reading R13).  y is m x n; returns N x n FP64."""
+    time, tp = _f64(time)
+    y, yp = _f32(y)
+    m, n = y.shape
+    out = np.empty((N, n), np.float64)
+    rc = _load().oracle_interp_perturbation(m, n, tp, yp, n, N, out.ctypes.data_as(_dp))
+    if rc != 0:
+        raise ValueError("oracle_interp_perturbation rejected its arguments")
+    return out
 
 
 def hilbert_noda(d1: np.ndarray, d2: np.ndarray):

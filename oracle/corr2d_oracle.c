@@ -39,6 +39,9 @@
  *  R12 Spectral-axis preprocessing: linear interpolation onto
  *      x_k = x_0 + k (x_last - x_0)/(n_out - 1), k = 0..n_out-1, last point
  *      set to x_last exactly; x must be strictly increasing.
+ *  R13 Perturbation-axis interpolation (Sec. 4.2) with the linear function
+ *      (approxfun); the package's default splinefun is not specified further
+ *      in the paper and is not stated here.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -275,6 +278,39 @@ int oracle_interp_linear(int m, int n_raw, const double* x_raw, const float* y_r
       double val = ya + t * (yb - ya);
       y_out[(long)j * n_out + k] = val;
       if (dyn_out) dyn_out[(long)j * n_out + k] = val - (ref ? (double)ref[k] : 0.0);
+    }
+  }
+  return 0;
+}
+
+/*
+ * Interpolation along the perturbation axis (Sec. 4.2, interpolation
+ * snippet): new perturbation values T_k = seq(min(Time), max(Time),
+ * length.out = N), i.e. T_k = t_0 + k (t_last - t_0)/(N - 1) with the last
+ * value t_last exactly, then every spectral variable (column nu of the m x n
+ * matrix) is evaluated at the T_k through an interpolating function of its
+ * values over Time.  The package offers approxfun (linear) and splinefun; the
+ * linear function is the one stated here (reading R13).  Time must be
+ * strictly increasing.  Output: N x n row-major.  Returns 0, or 1 on invalid
+ * arguments.
+ */
+int oracle_interp_perturbation(int m, int n, const double* time, const float* y, long ld, int N,
+                               double* out) {
+  if (m < 2 || n < 1 || N < 2 || !time || !y || !out || ld < n) return 1;
+  for (int j = 1; j < m; ++j)
+    if (!(time[j] > time[j - 1])) return 1;
+  double t0 = time[0], t1 = time[m - 1];
+  double step = (t1 - t0) / (double)(N - 1);
+  int seg = 0;
+  for (int k = 0; k < N; ++k) {
+    double T = (k == N - 1) ? t1 : t0 + (double)k * step;
+    while (seg < m - 2 && time[seg + 1] < T) ++seg;
+    double ta = time[seg], tb = time[seg + 1];
+    double u = (T - ta) / (tb - ta);
+    for (int v = 0; v < n; ++v) {
+      double ya = (double)y[(long)seg * ld + v];
+      double yb = (double)y[(long)(seg + 1) * ld + v];
+      out[(long)k * n + v] = ya + u * (yb - ya);
     }
   }
   return 0;

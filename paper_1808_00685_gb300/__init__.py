@@ -38,7 +38,7 @@ EXPORTED_SYMBOLS = (
     "corr2d_params_default", "corr2d_create", "corr2d_destroy", "corr2d_set_stream",
     "corr2d_last_error", "corr2d_synchronize", "corr2d_preprocess", "corr2d_compute",
     "corr2d_compute_host", "corr2d_batch", "corr2d_version", "corr2d_set_profiling",
-    "corr2d_get_timings", "corr2d_compute_noalloc",
+    "corr2d_get_timings", "corr2d_compute_noalloc", "corr2d_preprocess_perturbation",
 )
 
 
@@ -83,6 +83,7 @@ def load(path: str | None = None):
             "corr2d_last_error": (ctypes.c_char_p, [vp]),
             "corr2d_synchronize": (i, [vp]),
             "corr2d_preprocess": (i, [vp, i, i, vp, vp, i, vp, vp, vp]),
+            "corr2d_preprocess_perturbation": (i, [vp, i, i, vp, vp, i, i, vp]),
             "corr2d_compute": (i, [vp, i, i, vp, i, i, vp, i, ctypes.POINTER(corr2d_params), vp,
                                    vp, ctypes.c_long, vp, vp]),
             "corr2d_compute_host": (i, [vp, i, i, vp, i, vp, ctypes.POINTER(corr2d_params), vp,
@@ -140,6 +141,10 @@ def corr2d_set_stream(ctx: int, stream: int | None) -> None:
 
 def corr2d_synchronize(ctx: int) -> None:
     _check(ctx, load().corr2d_synchronize(ctx))
+
+
+def corr2d_preprocess_perturbation(ctx, m, n, time, y, ld, N, y_out) -> None:
+    _check(ctx, load().corr2d_preprocess_perturbation(ctx, m, n, time, y, ld, N, y_out))
 
 
 def corr2d_preprocess(ctx, m, n_raw, x_raw, y_raw, n_out, y_out, ref=None, dyn_out=None) -> None:
@@ -286,6 +291,15 @@ class Context:
         if want_sigma:
             return res + (s1, s2 if s2 is not None else s1)
         return res
+
+    def preprocess_perturbation(self, time, y, N):
+        """Resample the m x n stack y along the perturbation axis onto N equidistant steps."""
+        import torch
+        m, n = y.shape
+        out = torch.empty((N, n), dtype=torch.float32, device=y.device)
+        corr2d_preprocess_perturbation(self.handle, m, n, _ptr(time), _ptr(y), y.stride(0), N,
+                                       _ptr(out))
+        return out
 
     def preprocess(self, x_raw, y_raw, n_out, ref=None):
         import torch

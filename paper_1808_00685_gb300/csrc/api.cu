@@ -714,6 +714,21 @@ corr2d_status corr2d_synchronize(corr2d_ctx* ctx) {
   return CORR2D_OK;
 }
 
+corr2d_status corr2d_preprocess_perturbation(corr2d_ctx* ctx, int m, int n, const double* time,
+                                             const float* y, int ld, int N, float* y_out) {
+  if (!ctx) return CORR2D_EINVAL;
+  if (m < 2 || n < 1 || N < 2 || ld < n)
+    return fail(ctx, CORR2D_EINVAL, "perturbation interpolation needs m >= 2, n >= 1, N >= 2, ld >= n");
+  if (!time || !y || !y_out) return fail(ctx, CORR2D_EINVAL, "NULL buffer");
+  if (N > 65535) return fail(ctx, CORR2D_EUNSUPPORTED, "N > 65535");
+  DeviceGuard g(ctx->device);
+  for (const void* q : {(const void*)time, (const void*)y, (const void*)y_out})
+    if (!is_device_ptr(q, ctx->device)) return fail(ctx, CORR2D_EINVAL, "buffers must be device memory");
+  CUDA_TRY(ctx, launch_interp_t(m, n, time, y, ld, N, y_out, ctx->d_err, ctx->stream));
+  ctx->err.clear();
+  return CORR2D_OK;
+}
+
 corr2d_status corr2d_preprocess(corr2d_ctx* ctx, int m, int n_raw, const double* x_raw,
                                 const float* y_raw, int n_out, float* y_out, const float* ref,
                                 float* dyn_out) {

@@ -147,6 +147,8 @@ cudaError_t launch_xspec_simt(int kp1, int n1, int n2, const float* yr1, const f
 // Preprocessing.
 cudaError_t launch_interp(int m, int n_raw, const double* x, const float* y, int n_out,
                           float* out, const float* ref, float* dyn, int* err, cudaStream_t s);
+cudaError_t launch_interp_t(int m, int n, const double* t, const float* y, long ld, int N,
+                            float* out, int* err, cudaStream_t s);
 
 // Codes of the device error word: a bounded wait ran out, or the
 // preprocessing axis check failed.

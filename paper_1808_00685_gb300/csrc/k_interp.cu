@@ -58,6 +58,40 @@ __global__ void __launch_bounds__(128) k_interp(int m, int n_raw, const double* 
   }
 }
 
+// Interpolation along the perturbation axis (Sec. 4.2: new perturbation values
+// seq(min(Time), max(Time), length.out = N), every spectral variable evaluated
+// there through a linear interpolating function of its values over Time).
+// One thread per (new step k, variable nu); the segment of Time containing
+// T_k is the same for all variables of a row, so reads and writes are
+// coalesced along nu.  Same explicitly rounded FP64 blend as k_interp.
+__global__ void __launch_bounds__(256) k_interp_t(int m, int n, const double* __restrict__ t,
+                                                  const float* __restrict__ y, long ld, int N,
+                                                  float* __restrict__ out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (v >= n) return;
+  const double t0 = t[0], t1 = t[m - 1];
+  const double step = __ddiv_rn(__dsub_rn(t1, t0), (double)(N - 1));
+  const double T = (k == N - 1) ? t1 : __dadd_rn(t0, __dmul_rn((double)k, step));
+  int lo = 0, hi = m - 2;  // largest s in [0, m-2] with t[s] < T (0 if none)
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t[mid] < T) lo = mid; else hi = mid - 1;
+  }
+  const double ta = t[lo], tb = t[lo + 1];
+  const double u = __ddiv_rn(__dsub_rn(T, ta), __dsub_rn(tb, ta));
+  const double ya = (double)y[(size_t)lo * ld + v];
+  const double yb = (double)y[(size_t)(lo + 1) * ld + v];
+  out[(size_t)k * n + v] = (float)__dadd_rn(ya, __dmul_rn(u, __dsub_rn(yb, ya)));
+}
+
+cudaError_t launch_interp_t(int m, int n, const double* t, const float* y, long ld, int N,
+                            float* out, int* err, cudaStream_t s) {
+  k_check_axis<<<(m + 255) / 256, 256, 0, s>>>(m, t, err);
+  k_interp_t<<<dim3((n + 255) / 256, N), 256, 0, s>>>(m, n, t, y, ld, N, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_interp(int m, int n_raw, const double* x, const float* y, int n_out,
                           float* out, const float* ref, float* dyn, int* err, cudaStream_t s) {
   k_check_axis<<<(n_raw + 255) / 256, 256, 0, s>>>(n_raw, x, err);

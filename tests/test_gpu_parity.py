@@ -303,3 +303,28 @@ def test_host_buffer_entry_point(ctx):
     phi, psi = ctx.compute_host(torch.from_numpy(y1))
     ophi, opsi, _, _ = oracle.corr2d(y1)
     check(phi.double().numpy(), psi.double().numpy(), ophi, opsi, 1e-5, "host buffers homo")
+
+
+def test_preprocess_perturbation_bit_exact_and_feeds_compute(ctx):
+    """Sec. 4.2 perturbation-axis interpolation: uneven Time -> N equidistant steps,
+    bit-exact against the oracle, then the correlation of the resampled stack."""
+    rng = np.random.default_rng(12)
+    m, n, N = 100, 777, 128
+    time = np.sort(rng.uniform(0.0, 10.0, m))
+    time[0], time[-1] = 0.0, 10.0
+    y = workloads.sigmoid_bands(m, n, 15, seed=13)
+    out = ctx.preprocess_perturbation(dev(time), dev(y), N)
+    ctx.synchronize()
+    o = oracle.interp_perturbation(time, y, N)
+    assert np.array_equal(out.cpu().numpy(), o.astype(np.float32))
+    phi, psi = ctx.compute(out, precision="split", alpha=0.5)
+    ctx.synchronize()
+    ophi, opsi, _, _ = oracle.corr2d(o.astype(np.float32), alpha=0.5)
+    check(host(phi)[:, :n], host(psi)[:, :n], ophi, opsi, 1e-5, "interpolated along t")
+    bad = time.copy()
+    bad[5] = bad[4]
+    ctx.preprocess_perturbation(dev(bad), dev(y), N)
+    import paper_1808_00685_gb300 as pkg
+    with pytest.raises(pkg.Corr2dError) as ei:
+        ctx.synchronize()
+    assert ei.value.status == pkg.EINVAL

@@ -33,6 +33,8 @@ MUTATIONS = {
                          "for (int v = 0; v < n1; ++v) r1[v] = 0.0;"),
     "interp_weight": ("double t = (x - xa) / (xb - xa);", "double t = (x - xa) / (xb - x0);"),
     "psi_unscaled": ("psi[(long)r * n2 + b] = f * zi;", "psi[(long)r * n2 + b] = norm * zi;"),
+    "perturbation_grid": ("double step = (t1 - t0) / (double)(N - 1);",
+                          "double step = (t1 - t0) / (double)N;"),
 }
 
 
@@ -106,11 +108,19 @@ def _battery():
         return all(np.allclose(out[j], np.interp(g, x, yy[j].astype(np.float64)), atol=1e-12)
                    for j in range(2))
 
+    def interp_t_numpy():
+        t = np.sort(np.random.default_rng(5).uniform(0, 3, 9))
+        yy = workloads.random_stack(9, 3, seed=6)
+        out = oracle.interp_perturbation(t, yy, 13)
+        g = np.linspace(t[0], t[-1], 13)
+        return all(np.allclose(out[:, v], np.interp(g, t, yy[:, v].astype(np.float64)),
+                               atol=1e-12) for v in range(3))
+
     for name, fn in [("brute_homo", brute_homo), ("brute_hetero_odd", brute_hetero_odd),
                      ("brute_user_ref", brute_user_ref), ("parseval_even", parseval_even),
                      ("pearson_diag", pearson_diag), ("closed_form", closed_form),
                      ("dft_numpy", dft_numpy), ("sigma_numpy", sigma_numpy),
-                     ("interp_numpy", interp_numpy)]:
+                     ("interp_numpy", interp_numpy), ("interp_t_numpy", interp_t_numpy)]:
         check(name, fn)
     return failed
 

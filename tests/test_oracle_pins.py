@@ -398,6 +398,33 @@ def test_interp_reproduces_linear_functions_and_subtracts_reference():
     assert np.array_equal(dyn, out2 - ref.astype(np.float64))
 
 
+def test_perturbation_interp_matches_numpy_per_variable():
+    """Sec. 4.2: TIME <- seq(min(Time), max(Time), length.out = N), each column
+    evaluated through approxfun over Time (library special case: numpy.interp)."""
+    rng = np.random.default_rng(4)
+    time = np.sort(rng.uniform(0, 10, 12))
+    y = workloads.random_stack(12, 7, seed=2)
+    out = oracle.interp_perturbation(time, y, 16)
+    grid = np.linspace(time[0], time[-1], 16)
+    for v in range(7):
+        assert np.allclose(out[:, v], np.interp(grid, time, y[:, v].astype(np.float64)),
+                           rtol=0, atol=1e-12)
+    assert np.array_equal(out[0], y[0].astype(np.float64))
+    assert np.array_equal(out[-1], y[-1].astype(np.float64))
+
+
+def test_perturbation_interp_identity_and_linear_signal():
+    time = np.arange(9, dtype=np.float64) * 0.5
+    y = workloads.random_stack(9, 5, seed=3)
+    assert np.allclose(oracle.interp_perturbation(time, y, 9), y.astype(np.float64), atol=1e-15)
+    t = np.array([0.0, 0.3, 1.1, 2.0, 4.5])
+    lin = (2.0 + 3.0 * t)[:, None] * np.ones((1, 4))
+    out = oracle.interp_perturbation(t, lin.astype(np.float32), 10)
+    assert np.allclose(out, (2.0 + 3.0 * np.linspace(0, 4.5, 10))[:, None], atol=1e-5)
+    with pytest.raises(ValueError):
+        oracle.interp_perturbation(np.array([0.0, 1.0, 1.0]), np.zeros((3, 2), np.float32), 4)
+
+
 def test_interp_rejects_non_increasing_axis():
     x = np.array([0.0, 1.0, 1.0, 2.0])
     with pytest.raises(ValueError):
