@@ -913,10 +913,11 @@ corr2d_status corr2d_compute_host(corr2d_ctx* ctx, int m, int n1, const float* y
   int slab_tiles = (int)std::max<long>(1, std::min<long>(nt1, (256l << 20) / ((long)TILE_M * ld_dev * 8)));
   const size_t slab_bytes = align_up((size_t)slab_tiles * TILE_M * ld_dev * 4, 1024);
   if ((st = ensure(ctx, ctx->host_out, 4 * slab_bytes)) != CORR2D_OK) return st;
-  // Phi and Psi slabs go back on two streams (two copy engines)
-  cudaStream_t copy, copy2;
+  // Phi and Psi slabs go back on one copy stream (a second stream measured
+  // slower: the copies share one link)
+  cudaStream_t copy;
   CUDA_TRY(ctx, cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking));
-  CUDA_TRY(ctx, cudaStreamCreateWithFlags(&copy2, cudaStreamNonBlocking));
+  cudaStream_t copy2 = copy;
   cudaEvent_t done[2], freed[2], freed2[2];
   for (int i = 0; i < 2; ++i) {
     cudaEventCreateWithFlags(&freed2[i], cudaEventDisableTiming);
@@ -945,10 +946,17 @@ corr2d_status corr2d_compute_host(corr2d_ctx* ctx, int m, int n1, const float* y
     cudaEventRecord(done[sb], ctx->stream);
     cudaStreamWaitEvent(copy, done[sb], 0);
     cudaStreamWaitEvent(copy2, done[sb], 0);
-    cudaError_t e1 = cudaMemcpy2DAsync(phi + (size_t)t0 * TILE_M * ldo, ldo * 4, sphi, ld_dev * 4,
-                                       (size_t)n2 * 4, rows, cudaMemcpyDeviceToHost, copy);
-    cudaError_t e2 = cudaMemcpy2DAsync(psi + (size_t)t0 * TILE_M * ldo, ldo * 4, spsi, ld_dev * 4,
-                                       (size_t)n2 * 4, rows, cudaMemcpyDeviceToHost, copy2);
+    cudaError_t e1, e2;
+    if (ldo == ld_dev && ldo == n2) {  // contiguous slab: one linear copy per plane
+      const size_t bytes = (size_t)rows * n2 * 4;
+      e1 = cudaMemcpyAsync(phi + (size_t)t0 * TILE_M * ldo, sphi, bytes, cudaMemcpyDeviceToHost, copy);
+      e2 = cudaMemcpyAsync(psi + (size_t)t0 * TILE_M * ldo, spsi, bytes, cudaMemcpyDeviceToHost, copy2);
+    } else {
+      e1 = cudaMemcpy2DAsync(phi + (size_t)t0 * TILE_M * ldo, ldo * 4, sphi, ld_dev * 4,
+                             (size_t)n2 * 4, rows, cudaMemcpyDeviceToHost, copy);
+      e2 = cudaMemcpy2DAsync(psi + (size_t)t0 * TILE_M * ldo, ldo * 4, spsi, ld_dev * 4,
+                             (size_t)n2 * 4, rows, cudaMemcpyDeviceToHost, copy2);
+    }
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
       result = fail(ctx, CORR2D_ECUDA, "device-to-host copy failed: %s",
                     cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
@@ -967,7 +975,6 @@ corr2d_status corr2d_compute_host(corr2d_ctx* ctx, int m, int n1, const float* y
     release(slab_desc[i]);
   }
   cudaStreamDestroy(copy);
-  cudaStreamDestroy(copy2);
   (void)last;
   if (result != CORR2D_OK) return result;
   return corr2d_synchronize(ctx);

@@ -2,8 +2,9 @@
 // DFT along the perturbation axis (Eqs. ref, dynspec, stdev, disFT; the half
 // spectrum of Sec. 4.2), producing the operand rows of the cross-spectrum.
 //
-// Tensor-core kernel (k_prep_tc): one CTA of 512 threads per 128 spectral
-// variables; four threads share a variable's perturbation steps.
+// Tensor-core kernel (k_prep_tc): one CTA of 256 threads per 128 spectral
+// variables (two CTAs per SM); two threads share a variable's perturbation
+// steps.
 //   1. FP64 reference (perturbation mean or the caller's spectrum) from FP64
 //      partial sums; FP32 extremes of y give the range of y - ref.
 //   2. FP64 centering y - ref, rounded once to FP32, scaled by a power of two
@@ -14,7 +15,7 @@
 //      -sin of 2 pi ((omega j) mod m) / m, FP64-built, split likewise) into
 //      TMEM: D(nu, c) = sum_j y~(nu, j) W(c, j); with planes hi*hi + hi*lo +
 //      lo*hi.  The twiddle chunks arrive by bulk copy.
-//   4. Epilogue (16 warps, four per TMEM lane quadrant): row maximum,
+//   4. Epilogue (8 warps, two per TMEM lane quadrant): row maximum,
 //      power-of-two rescale, split into planes, operand rows (unweighted for
 //      stack 1, weight w = 1 / 2 for stack 2), scale sigma^-alpha 2^-E, sigma.
 // FP64 is kept to the mean and the centering subtraction: GB300's FP64 rate is
@@ -25,9 +26,20 @@
 
 namespace c2d {
 
-constexpr int PREP_THREADS = 512;
-constexpr int PREP_GROUPS = PREP_THREADS / PREP_ROWS;  // threads per variable
-constexpr int PREP_SCRATCH = PREP_GROUPS * PREP_ROWS * (8 + 4 + 4 + 4 + 4 + 4) + PREP_ROWS * 16;
+constexpr int PREP_THREADS = 256;
+constexpr int PREP_GROUPS = PREP_THREADS / PREP_ROWS;  // threads per variable (2)
+constexpr int PREP_JG = 8 / PREP_GROUPS;               // 8-step groups per thread per chunk
+// reduction scratch: FP64 sums (4 x 128), FP32 min / max / sum of squares
+// (3 x 4 x 128; the min slots are reused for the epilogue row maxima), per-row
+// exponent (128 ints) and reference (128 doubles)
+constexpr int PREP_SCRATCH = PREP_GROUPS * PREP_ROWS * (8 + 4 + 4 + 4) + PREP_ROWS * (4 + 8);
+
+// Error-free sum of two floats: a + b = s + e exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
 
 // 16 consecutive TMEM columns of this warp's lanes.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -102,7 +114,7 @@ __device__ __forceinline__ void store_chunk(uint8_t* dst, const float* re, const
 }
 
 template <int P>
-__global__ void __launch_bounds__(PREP_THREADS) k_prep_tc(const PrepJob* __restrict__ jobs,
+__global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __restrict__ jobs,
                                                           const PrepItem* __restrict__ items,
                                                           int* err, unsigned long long limit_ns) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -126,10 +138,10 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep_tc(const PrepJob* __restr
   float* red_mn = (float*)(red_s + PREP_GROUPS * PREP_ROWS);
   float* red_mx = red_mn + PREP_GROUPS * PREP_ROWS;
   float* red_ss = red_mx + PREP_GROUPS * PREP_ROWS;        // Kahan partials
-  float* red_max = red_ss + PREP_GROUPS * PREP_ROWS;       // epilogue row maxima
-  int* row_ey = (int*)(red_max + PREP_GROUPS * PREP_ROWS);      // 128 used, 512 reserved
-  double* row_ref = (double*)(row_ey + PREP_GROUPS * PREP_ROWS);
-  uint64_t* bars = (uint64_t*)(row_ref + PREP_ROWS);
+  float* red_max = red_mn;                                 // epilogue row maxima (reuse)
+  double* row_ref = (double*)(red_ss + PREP_GROUPS * PREP_ROWS);
+  int* row_ey = (int*)(row_ref + PREP_ROWS);
+  uint64_t* bars = (uint64_t*)(row_ey + PREP_ROWS);
   uint32_t* tmem_slot = (uint32_t*)(bars + 2);
   const uint32_t wbar = smem_u32(&bars[0]), mbar = smem_u32(&bars[1]);
   const uint32_t ncols = tmem_cols_for(ncomp);
@@ -157,12 +169,33 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep_tc(const PrepJob* __restr
           mx = fmaxf(mx, v);
         }
       } else {
-        for (int j = g; j < m; j += PREP_GROUPS) {
+        // FP64 accumulation of error-free FP32 partial sums: four values are
+        // summed exactly as s4 + e4 by TwoSum, s4 goes into the FP64 sum, the
+        // residuals e4 (each below half an ulp of s4) into a FP32 sum that
+        // joins the FP64 sum at the end.  One FP64 add per four values.
+        float res = 0.f;
+        int j = g;
+        for (; j + 3 * PREP_GROUPS < m; j += 4 * PREP_GROUPS) {
+          const float a = y[(long)j * ld + nu];
+          const float b = y[(long)(j + PREP_GROUPS) * ld + nu];
+          const float c = y[(long)(j + 2 * PREP_GROUPS) * ld + nu];
+          const float d = y[(long)(j + 3 * PREP_GROUPS) * ld + nu];
+          float s1, e1, s2, e2, s4, e3;
+          two_sum(a, b, s1, e1);
+          two_sum(c, d, s2, e2);
+          two_sum(s1, s2, s4, e3);
+          s += (double)s4;
+          res += (e1 + e2) + e3;
+          mn = fminf(fminf(mn, fminf(a, b)), fminf(c, d));
+          mx = fmaxf(fmaxf(mx, fmaxf(a, b)), fmaxf(c, d));
+        }
+        for (; j < m; j += PREP_GROUPS) {
           const float v = y[(long)j * ld + nu];
           s += (double)v;
           mn = fminf(mn, v);
           mx = fmaxf(mx, v);
         }
+        s += (double)res;
       }
     }
     red_s[g * PREP_ROWS + r] = s;
@@ -220,7 +253,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep_tc(const PrepJob* __restr
     }
     // this thread's two groups of 8 steps: jg = g and g + 4
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < PREP_JG; ++h) {
       const int jg = g + PREP_GROUPS * h;
       float v[8];
 #pragma unroll
@@ -275,15 +308,15 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep_tc(const PrepJob* __restr
   ok = ok && mbar_wait(mbar, (jchunks - 1) & 1, wc);
   tc_fence_after();
 
-  // ---- 4. epilogue: 16 warps, warp w reads TMEM lane quadrant q = w % 4 and
-  // column part w / 4
+  // ---- 4. epilogue: warp w reads TMEM lane quadrant q = w % 4 and column
+  // part w / 4 (PREP_GROUPS parts)
   const int q = warp & 3, part = warp >> 2;
   const int lr = q * 32 + lane;                       // tile row (TMEM lane)
   const int nu_e = item.tile * PREP_ROWS + lr;
   const bool valid_e = nu_e < n;
   const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
   float dmax = 0.f;
-  for (int b = part; b < ncomp / 16; b += 4) {
+  for (int b = part; b < ncomp / 16; b += PREP_GROUPS) {
     float v[16];
     tmem_ld16(trow + b * 16, v);
 #pragma unroll
@@ -291,8 +324,8 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep_tc(const PrepJob* __restr
   }
   red_max[part * PREP_ROWS + lr] = dmax;
   __syncthreads();
-  dmax = fmaxf(fmaxf(red_max[lr], red_max[PREP_ROWS + lr]),
-               fmaxf(red_max[2 * PREP_ROWS + lr], red_max[3 * PREP_ROWS + lr]));
+  dmax = red_max[lr];
+  for (int k = 1; k < PREP_GROUPS; ++k) dmax = fmaxf(dmax, red_max[k * PREP_ROWS + lr]);
   int eY = 0;
   if (dmax > 0.f) {
     int e;
@@ -304,7 +337,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep_tc(const PrepJob* __restr
   const int nch = kp / gsz;
   uint8_t* rowA = (job.outA && valid_e) ? (uint8_t*)(job.outA + (size_t)nu_e * job.rowlen) : nullptr;
   uint8_t* rowB = (job.outB && valid_e) ? (uint8_t*)(job.outB + (size_t)nu_e * job.rowlen) : nullptr;
-  for (int c = part; c < nch; c += 4) {
+  for (int c = part; c < nch; c += PREP_GROUPS) {
     float re[32], im[32];
     if (P == 2) {
       float a[16], b[16];
