@@ -86,6 +86,12 @@ typedef enum {
  *   z~2 = N y~2 with the Hilbert-Noda matrix N_jk = 1/(pi (k - j)), N_jj = 0,
  * default Norm 1/(m - 1).  Tensor-core precisions only, m <= 256. */
 #define CORR2D_FLAG_HILBERT 4u
+/* Homo correlation: store only the upper triangle (nu2 >= nu1) of Phi and Psi,
+ * the half that determines the rest (Phi symmetric, Psi antisymmetric); half
+ * the output traffic.  Elements with nu2 < nu1 are unspecified: those within
+ * 32 rows of the diagonal hold their mirrored values, the others are not
+ * written.  Ignored for hetero problems. */
+#define CORR2D_FLAG_UPPER_TRIANGLE 8u
 
 typedef struct {
   int ref_mode;       /* corr2d_ref_mode */
@@ -179,6 +185,22 @@ corr2d_status corr2d_preprocess_perturbation(corr2d_ctx* ctx, int m, int n, cons
 corr2d_status corr2d_compute(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1, int n2,
                              const float* y2, int ld2, const corr2d_params* params, float* phi,
                              float* psi, long ldo, float* sigma1_out, float* sigma2_out);
+
+/*
+ * One row slab of the correlation: output rows nu1 in [row_begin, row_begin +
+ * row_count) of Phi and Psi, written to phi/psi as a row_count x n2 matrix
+ * (leading dimension ldo).  Slabs are independent -- this is how the work is
+ * split over several GPUs (one context and slab per GPU, no communication):
+ * every slab needs both whole stacks and recomputes their DFT, which is cheap
+ * next to the n1 x n2 output.  row_begin must be a multiple of 128 (the tile
+ * height); row_count >= 1 with row_begin + row_count <= n1.  Tensor-core
+ * precisions; all tiles of the slab are computed (no mirroring).  Other
+ * arguments as corr2d_compute.
+ */
+corr2d_status corr2d_compute_rows(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1,
+                                  int n2, const float* y2, int ld2, const corr2d_params* params,
+                                  int row_begin, int row_count, float* phi, float* psi,
+                                  long ldo);
 
 /*
  * Same computation with every buffer in HOST memory: the library copies the

@@ -32,6 +32,7 @@ REF_MEAN, REF_USER = 0, 1
 FLAG_NO_MIRROR = 1
 FLAG_EXACT_SYMMETRY = 2
 FLAG_HILBERT = 4
+FLAG_UPPER_TRIANGLE = 8
 _PREC_BY_NAME = {"fp32": PREC_FP32, "split": PREC_SPLIT, "bf16": PREC_BF16}
 
 EXPORTED_SYMBOLS = (
@@ -39,6 +40,7 @@ EXPORTED_SYMBOLS = (
     "corr2d_last_error", "corr2d_synchronize", "corr2d_preprocess", "corr2d_compute",
     "corr2d_compute_host", "corr2d_batch", "corr2d_version", "corr2d_set_profiling",
     "corr2d_get_timings", "corr2d_compute_noalloc", "corr2d_preprocess_perturbation",
+    "corr2d_compute_rows",
 )
 
 
@@ -84,6 +86,8 @@ def load(path: str | None = None):
             "corr2d_synchronize": (i, [vp]),
             "corr2d_preprocess": (i, [vp, i, i, vp, vp, i, vp, vp, vp]),
             "corr2d_preprocess_perturbation": (i, [vp, i, i, vp, vp, i, i, vp]),
+            "corr2d_compute_rows": (i, [vp, i, i, vp, i, i, vp, i, ctypes.POINTER(corr2d_params),
+                                        i, i, vp, vp, ctypes.c_long]),
             "corr2d_compute": (i, [vp, i, i, vp, i, i, vp, i, ctypes.POINTER(corr2d_params), vp,
                                    vp, ctypes.c_long, vp, vp]),
             "corr2d_compute_host": (i, [vp, i, i, vp, i, vp, ctypes.POINTER(corr2d_params), vp,
@@ -158,6 +162,24 @@ def corr2d_compute(ctx, m, n1, y1, ld1, n2, y2, ld2, params, phi, psi, ldo, sigm
                                       sigma1, sigma2))
 
 
+def corr2d_compute_rows(ctx, m, n1, y1, ld1, n2, y2, ld2, params, row_begin, row_count, phi,
+                        psi, ldo) -> None:
+    pp = ctypes.byref(params) if params is not None else None
+    _check(ctx, load().corr2d_compute_rows(ctx, m, n1, y1, ld1, n2, y2, ld2, pp, row_begin,
+                                           row_count, phi, psi, ldo))
+
+
+def shard_rows(n1: int, world: int, rank: int, tile: int = 128):
+    """Row slab (row_begin, row_count) of rank `rank` when the n1 output rows are
+    split over `world` GPUs in whole 128-row tiles (corr2d_compute_rows)."""
+    ntiles = (n1 + tile - 1) // tile
+    per, extra = divmod(ntiles, world)
+    t0 = rank * per + min(rank, extra)
+    t1 = t0 + per + (1 if rank < extra else 0)
+    r0, r1 = t0 * tile, min(n1, t1 * tile)
+    return r0, max(0, r1 - r0)
+
+
 def corr2d_compute_host(ctx, m, n1, y1, n2, y2, params, phi, psi, ldo) -> None:
     pp = ctypes.byref(params) if params is not None else None
     _check(ctx, load().corr2d_compute_host(ctx, m, n1, y1, n2, y2, pp, phi, psi, ldo))
@@ -203,7 +225,8 @@ def _ptr(t):
 
 
 def make_params(precision="split", alpha=0.0, norm=0.0, ref1=None, ref2=None,
-                no_mirror=False, exact_symmetry=False, hilbert=False) -> corr2d_params:
+                no_mirror=False, exact_symmetry=False, hilbert=False,
+                upper_triangle=False) -> corr2d_params:
     p = corr2d_params_default()
     p.precision = _PREC_BY_NAME[precision] if isinstance(precision, str) else int(precision)
     p.alpha = float(alpha)
@@ -213,7 +236,7 @@ def make_params(precision="split", alpha=0.0, norm=0.0, ref1=None, ref2=None,
         p.ref1 = _ptr(ref1)
         p.ref2 = _ptr(ref2)
     p.flags = ((FLAG_NO_MIRROR if no_mirror else 0) | (FLAG_EXACT_SYMMETRY if exact_symmetry else 0)
-               | (FLAG_HILBERT if hilbert else 0))
+               | (FLAG_HILBERT if hilbert else 0) | (FLAG_UPPER_TRIANGLE if upper_triangle else 0))
     return p
 
 
@@ -266,7 +289,7 @@ class Context:
 
     def compute(self, y1, y2=None, precision="split", alpha=0.0, norm=0.0, ref1=None, ref2=None,
                 no_mirror=False, out=None, want_sigma=False, exact_symmetry=False,
-                hilbert=False):
+                hilbert=False, upper_triangle=False):
         """Phi, Psi (n1 x n2 views) of the m x n1 stack y1 (and y2, or homo)."""
         import torch
         assert y1.is_cuda and y1.dtype == torch.float32 and y1.dim() == 2
@@ -283,7 +306,7 @@ class Context:
         s2 = (torch.empty(n2, dtype=torch.float32, device=y1.device)
               if (want_sigma and y2 is not None) else None)
         params = make_params(precision, alpha, norm, ref1, ref2, no_mirror, exact_symmetry,
-                             hilbert)
+                             hilbert, upper_triangle)
         corr2d_compute(self.handle, m, n1, _ptr(y1), y1.stride(0), n2, _ptr(y2),
                        y2.stride(0) if y2 is not None else 0, params, _ptr(phi), _ptr(psi), ldo,
                        _ptr(s1), _ptr(s2))
@@ -321,6 +344,18 @@ class Context:
                                      phi.stride(0)))
         corr2d_batch(self.handle, ps, make_params(precision, alpha, norm, None, None, no_mirror,
                                                   hilbert=hilbert))
+
+    def compute_rows(self, y1, y2, row_begin, row_count, precision="split", alpha=0.0, norm=0.0,
+                     hilbert=False):
+        """Rows [row_begin, row_begin + row_count) of Phi and Psi (row_begin % 128 == 0)."""
+        m, n1 = y1.shape
+        n2 = n1 if y2 is None else y2.shape[1]
+        phi, psi, ldo = self.alloc_out(row_count, n2, y1.device)
+        params = make_params(precision, alpha, norm, hilbert=hilbert)
+        corr2d_compute_rows(self.handle, m, n1, _ptr(y1), y1.stride(0), n2, _ptr(y2),
+                            y2.stride(0) if y2 is not None else 0, params, row_begin, row_count,
+                            _ptr(phi), _ptr(psi), ldo)
+        return phi[:, :n2], psi[:, :n2]
 
     def compute_host(self, y1, y2=None, precision="split", alpha=0.0, norm=0.0, out=None):
         """Host (CPU) tensors in and out; copies overlap the kernels inside the library."""

@@ -445,6 +445,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   xp.mirror = (homo && tc.mirror && tc.bn == TILE_M) ? 1 : 0;
   xp.bn = tc.bn;
   xp.out_row_tile0 = out_row_tile0;
+  xp.upper_only = (xp.mirror && (p.flags & CORR2D_FLAG_UPPER_TRIANGLE)) ? 1 : 0;
   std::vector<XProblem> probs{xp};
   std::vector<XItem> xitems;
   append_tiles(xitems, 0, n1, n2, tc.bn, xp.mirror != 0, ti_begin, ti_end, tc.group);
@@ -799,7 +800,8 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
   auto key = std::make_tuple(m, n1, n2e, homo ? 1 : 0,
                              p.precision * 8 + (int)(p.flags & (CORR2D_FLAG_NO_MIRROR |
                                                                 CORR2D_FLAG_EXACT_SYMMETRY |
-                                                                CORR2D_FLAG_HILBERT)));
+                                                                CORR2D_FLAG_HILBERT |
+                                                                CORR2D_FLAG_UPPER_TRIANGLE)));
   auto it = ctx->tuned.find(key);
   if (it != ctx->tuned.end()) { *out = it->second; return CORR2D_OK; }
   std::vector<TileChoice> cands;
@@ -809,7 +811,7 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
     cands.push_back(TileChoice{128, 1, 8});
     cands.push_back(TileChoice{128, 1, 12});
   }
-  if (!(can_mirror && (p.flags & CORR2D_FLAG_EXACT_SYMMETRY))) {
+  if (!(can_mirror && (p.flags & (CORR2D_FLAG_EXACT_SYMMETRY | CORR2D_FLAG_UPPER_TRIANGLE)))) {
     cands.push_back(TileChoice{128, 0, 0});
     cands.push_back(TileChoice{128, 0, 12});
     cands.push_back(TileChoice{64, 0, 0});
@@ -881,6 +883,32 @@ corr2d_status corr2d_compute(corr2d_ctx* ctx, int m, int n1, const float* y1, in
     CUDA_TRY(ctx, cudaMemcpyAsync(sigma2_out, sigma1_out, (size_t)n1 * 4, cudaMemcpyDeviceToDevice, ctx->stream));
   else if (homo && sigma2_out)
     return fail(ctx, CORR2D_EINVAL, "homo correlation: pass sigma1_out to get sigma2_out");
+  ctx->err.clear();
+  return CORR2D_OK;
+}
+
+corr2d_status corr2d_compute_rows(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1,
+                                  int n2, const float* y2, int ld2, const corr2d_params* params,
+                                  int row_begin, int row_count, float* phi, float* psi,
+                                  long ldo) {
+  if (!ctx) return CORR2D_EINVAL;
+  corr2d_params p;
+  if (params) p = *params; else corr2d_params_default(&p);
+  DeviceGuard g(ctx->device);
+  corr2d_status st = validate_compute(ctx, m, n1, y1, ld1, n2, y2, ld2, p, phi, psi, ldo, true);
+  if (st != CORR2D_OK) return st;
+  if (p.precision == CORR2D_PREC_FP32)
+    return fail(ctx, CORR2D_EUNSUPPORTED, "row slabs run the tensor-core precisions");
+  if (row_begin < 0 || row_begin % TILE_M != 0 || row_count < 1 || row_begin + row_count > n1)
+    return fail(ctx, CORR2D_EINVAL, "row slab [%d, %d) must start at a multiple of %d inside [0, %d)",
+                row_begin, row_begin + row_count, TILE_M, n1);
+  const bool homo = (y2 == nullptr);
+  if (homo) { n2 = n1; ld2 = ld1; }
+  TileChoice tc{128, 0, 0};
+  const int t0 = row_begin / TILE_M, t1 = (row_begin + row_count + TILE_M - 1) / TILE_M;
+  st = enqueue_tc(ctx, m, n1, y1, ld1, n2, homo ? nullptr : y2, ld2, p, phi, psi, ldo, row_count,
+                  nullptr, nullptr, tc, t0, t1, t0, false, ctx->ops, ctx->desc, ctx->desc_host);
+  if (st != CORR2D_OK) return st;
   ctx->err.clear();
   return CORR2D_OK;
 }
@@ -1092,6 +1120,7 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
       xp.mirror = (homo && bn == 128 && !(p.flags & CORR2D_FLAG_NO_MIRROR)) ? 1 : 0;
       xp.bn = bn;
       xp.out_row_tile0 = 0;
+      xp.upper_only = (xp.mirror && (p.flags & CORR2D_FLAG_UPPER_TRIANGLE)) ? 1 : 0;
       probs.push_back(xp);
     }
     // tiles, longest first (more chunks = more MMA work), stable within a problem

@@ -95,7 +95,8 @@ struct alignas(128) XProblem {
   int mirror;          // 1: homo tile with its mirror written too (bn == 128)
   int bn;              // nu2 columns per tile: 64 or 128
   int out_row_tile0;   // output rows are shifted up by out_row_tile0 * 128
-  int pad_[3];
+  int upper_only;      // 1: mirrored problem storing only nu2 >= nu1 (no mirror boxes)
+  int pad_[2];
 };
 
 // One tile of the cross-spectrum kernel: problem index and tile coordinates.

@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
     const CUtensorMap* tm = nullptr;
     const float* s1p = nullptr;
     const float* s2p = nullptr;
-    int n1 = 0, n2 = 0, bn = 0, pmirror = 0, orow_off = 0;
+    int n1 = 0, n2 = 0, bn = 0, pmirror = 0, orow_off = 0, upper = 0;
     float norm = 0.f;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++lt) {
       const XItem w = items[it];
@@ -213,6 +213,7 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
         n2 = pr->n2;
         bn = pr->bn;
         pmirror = pr->mirror;
+        upper = pr->upper_only;
         orow_off = pr->out_row_tile0 * TILE_M;
         norm = pr->norm;
       }
@@ -251,7 +252,8 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
       for (int cc = diag ? q : 0; cc < nbox; ++cc) {
         const int col0 = colt + cc * 32;
         if (col0 >= n2) break;  // warp-uniform
-        const bool mirror = pmirror && (!diag || cc > q);
+        // upper-triangle output: no mirrored boxes (diagonal boxes stay whole)
+        const bool mirror = pmirror && !upper && (!diag || cc > q);
         const bool tri = diag && cc == q;
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + half * 128 + cc * 32),

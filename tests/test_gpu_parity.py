@@ -328,3 +328,50 @@ def test_preprocess_perturbation_bit_exact_and_feeds_compute(ctx):
     with pytest.raises(pkg.Corr2dError) as ei:
         ctx.synchronize()
     assert ei.value.status == pkg.EINVAL
+
+
+def test_row_slabs_assemble_the_full_result(ctx):
+    """Multi-GPU layout on one GPU: the rows split into 128-aligned slabs (one per
+    would-be GPU), each computed independently, equal one full call bit for bit."""
+    import paper_1808_00685_gb300 as pkg
+    y1 = workloads.random_stack(50, 700, seed=21)
+    y2 = workloads.random_stack(50, 333, seed=22)
+    d1, d2 = dev(y1), dev(y2)
+    full = run(ctx, y1, y2, precision="split")
+    for world in (2, 3):
+        parts_phi, parts_psi = [], []
+        for rank in range(world):
+            r0, cnt = pkg.shard_rows(700, world, rank)
+            ph, ps = ctx.compute_rows(d1, d2, r0, cnt)
+            ctx.synchronize()
+            parts_phi.append(host(ph))
+            parts_psi.append(host(ps))
+        phi = np.concatenate(parts_phi)
+        psi = np.concatenate(parts_psi)
+        # same arithmetic per element; the full call's tuned tile width may differ
+        assert rel(phi, full[0]) < 1e-6 and rel(psi, full[1]) < 1e-6
+        ophi, opsi, _, _ = oracle.corr2d(y1, y2)
+        check(phi, psi, ophi, opsi, 1e-5, f"{world} row slabs")
+    with pytest.raises(pkg.Corr2dError):
+        ctx.compute_rows(d1, d2, 100, 10)  # not a multiple of 128
+
+
+def test_upper_triangle_output(ctx):
+    """CORR2D_FLAG_UPPER_TRIANGLE: nu2 >= nu1 equals the full result; lower boxes
+    away from the diagonal are not written (sentinel NaNs stay)."""
+    import paper_1808_00685_gb300 as pkg
+    n = 700
+    y = workloads.random_stack(40, n, seed=23)
+    d = dev(y)
+    full = run(ctx, y, precision="split", exact_symmetry=True)
+    phi, psi, ldo = pkg.Context.alloc_out(n, n, d.device)
+    phi.fill_(float("nan"))
+    psi.fill_(float("nan"))
+    ph, ps = ctx.compute(d, out=(phi, psi), upper_triangle=True)
+    ctx.synchronize()
+    ph, ps = host(ph)[:, :n], host(ps)[:, :n]
+    iu = np.triu_indices(n)
+    assert np.array_equal(ph[iu], full[0][iu]) and np.array_equal(ps[iu], full[1][iu])
+    r, c = np.indices((n, n))
+    far_lower = (r // 32) > (c // 32)
+    assert np.all(np.isnan(ph[far_lower])) and np.all(np.isnan(ps[far_lower]))

@@ -47,3 +47,15 @@ def test_reference_arm_under_torchrun_prints_once():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_row_shards_cover_every_row_once():
+    import paper_1808_00685_gb300 as pkg
+    for n1 in (1, 127, 128, 129, 700, 32768):
+        for world in (1, 2, 3, 4, 8):
+            rows = []
+            for rank in range(world):
+                r0, cnt = pkg.shard_rows(n1, world, rank)
+                assert r0 % 128 == 0 or cnt == 0
+                rows.extend(range(r0, r0 + cnt))
+            assert rows == list(range(n1))
