@@ -1134,7 +1134,7 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
                    (probs[i].n1 + TILE_M - 1) / TILE_M);
     return CORR2D_OK;
   };
-  auto make_graph = [&](int bn_threshold, cudaGraphExec_t* exec,
+  auto make_graph = [&](int bn_threshold, int chunk, cudaGraphExec_t* exec,
                         cudaGraphExec_t* exec_x) -> corr2d_status {
     std::vector<PrepJob> jobs;
     std::vector<PrepItem> pitems;
@@ -1160,7 +1160,8 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
       e5 = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (e5 == cudaSuccess) {
         e2 = launch_xspec_tc((const XProblem*)(d + b.off_probs), (const XItem*)(d + b.off_xitems),
-                             b.nxitems, planes, ctx->sm_count, ctx->d_err, ctx->limit_ns, cs);
+                             b.nxitems, planes, ctx->sm_count, ctx->d_err, ctx->limit_ns, cs, 0,
+                             chunk);
         e5 = cudaStreamEndCapture(cs, &graph_x);
       }
     }
@@ -1182,16 +1183,19 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
   if (bc.exec) { cudaGraphExecDestroy(bc.exec); bc.exec = nullptr; }
   if (bc.exec_x) { cudaGraphExecDestroy(bc.exec_x); bc.exec_x = nullptr; }
   // tuner: time the batch graph for each tile-width threshold, keep the fastest
+  // tuner: tile width (bn = 64 below a problem size) x run length per CTA
   const int thresholds[] = {0, 1024, 2048};
-  int best_thr = 0;
+  const int chunks[] = {1, 4};
+  int best_thr = 0, best_chunk = 1;
   if (!getenv("CORR2D_NO_TUNE")) {
     cudaEvent_t e0, e1;
     CUDA_TRY(ctx, cudaEventCreate(&e0));
     CUDA_TRY(ctx, cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int thr : thresholds) {
+    for (int cand = 0; cand < 6; ++cand) {
+      const int thr = thresholds[cand % 3], chunk = chunks[cand / 3];
       cudaGraphExec_t ex = nullptr, exx = nullptr;
-      if ((st = make_graph(thr, &ex, &exx)) != CORR2D_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+      if ((st = make_graph(thr, chunk, &ex, &exx)) != CORR2D_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
       float ms = 0.f;
       for (int rep = 0; rep < 2; ++rep) {
         cudaEventRecord(e0, ctx->stream);
@@ -1204,13 +1208,14 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
       cudaGraphExecDestroy(ex);
       cudaGraphExecDestroy(exx);
       if (getenv("CORR2D_VERBOSE"))
-        fprintf(stderr, "corr2d batch tuner: bn=64 below n=%d -> %.4f ms\n", thr, ms);
-      if (ms < best) { best = ms; best_thr = thr; }
+        fprintf(stderr, "corr2d batch tuner: bn=64 below n=%d, runs of %d -> %.4f ms\n", thr,
+                chunk, ms);
+      if (ms < best) { best = ms; best_thr = thr; best_chunk = chunk; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
-  if ((st = make_graph(best_thr, &bc.exec, &bc.exec_x)) != CORR2D_OK) return st;
+  if ((st = make_graph(best_thr, best_chunk, &bc.exec, &bc.exec_x)) != CORR2D_OK) return st;
   bc.key = key;
   CUDA_TRY(ctx, replay(bc.exec, bc.exec_x));
   ctx->recorded = ctx->profiling;

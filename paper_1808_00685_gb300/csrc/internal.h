@@ -119,10 +119,11 @@ cudaError_t init_xspec_kernels();
 cudaError_t launch_prep_tc(const PrepJob* d_jobs, const PrepItem* d_items, int nitems, int planes,
                            int max_kp, int* err, unsigned long long limit_ns, cudaStream_t s);
 // inject & 1 makes the producer issue nothing (host-requested fault for the
-// time-out test); 0 in normal operation.
+// time-out test); 0 in normal operation.  Each CTA takes runs of `chunk`
+// consecutive work items.
 cudaError_t launch_xspec_tc(const XProblem* d_probs, const XItem* d_items, int nitems,
                             int planes, int grid, int* err, unsigned long long limit_ns,
-                            cudaStream_t s, int inject = 0);
+                            cudaStream_t s, int inject = 0, int chunk = 1);
 
 // FP32 CUDA-core path.
 struct SimtPrepJob {
