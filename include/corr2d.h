@@ -187,6 +187,22 @@ corr2d_status corr2d_compute(corr2d_ctx* ctx, int m, int n1, const float* y1, in
                              float* psi, long ldo, float* sigma1_out, float* sigma2_out);
 
 /*
+ * Reduced map for display (Sec. 4.3: plot_corr2din3d's `reduce` argument
+ * resamples the matrix at the 1-based indices divisible by `reduce` with a
+ * box kernel, i.e. it keeps every reduce-th row and column).  Computes
+ *   phi_r[i][j] = Phi(nu1 = reduce (i + 1) - 1, nu2 = reduce (j + 1) - 1)
+ * (and psi_r alike) for i < n1 / reduce, j < n2 / reduce, directly: only the
+ * sampled variables are transformed and correlated, so the full n1 x n2 map
+ * is never formed.  The reference, sigma and scaling of each sampled variable
+ * are those of the full problem.  reduce >= 1; ldr >= n2 / reduce, a multiple
+ * of 4; tensor-core precisions.  Other arguments as corr2d_compute.
+ */
+corr2d_status corr2d_compute_reduced(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1,
+                                     int n2, const float* y2, int ld2,
+                                     const corr2d_params* params, int reduce, float* phi_r,
+                                     float* psi_r, long ldr);
+
+/*
  * One row slab of the correlation: output rows nu1 in [row_begin, row_begin +
  * row_count) of Phi and Psi, written to phi/psi as a row_count x n2 matrix
  * (leading dimension ldo).  Slabs are independent -- this is how the work is

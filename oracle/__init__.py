@@ -300,6 +300,19 @@ def interp_perturbation(time: np.ndarray, y: np.ndarray, N: int) -> np.ndarray:
     return out
 
 
+def reduce_map(M: np.ndarray, reduce: int) -> np.ndarray:
+    """plot_corr2din3d's `reduce` (Sec. 4.3, reading R14): rows and columns whose
+    1-based index i satisfies i %% reduce == 0, sampled with a box kernel at those
+    grid points, i.e. their values themselves."""
+    rows = [i - 1 for i in range(1, M.shape[0] + 1) if i % reduce == 0]
+    cols = [j - 1 for j in range(1, M.shape[1] + 1) if j % reduce == 0]
+    out = np.empty((len(rows), len(cols)), dtype=M.dtype)
+    for a, i in enumerate(rows):
+        for b, j in enumerate(cols):
+            out[a, b] = M[i, j]
+    return out
+
+
 def hilbert_noda(d1: np.ndarray, d2: np.ndarray):
     """Hilbert-transform approach on dynamic spectra (Eqs. disHTsyn..disHTasyn)."""
     d1, q1 = _f64(d1)

@@ -40,7 +40,7 @@ EXPORTED_SYMBOLS = (
     "corr2d_last_error", "corr2d_synchronize", "corr2d_preprocess", "corr2d_compute",
     "corr2d_compute_host", "corr2d_batch", "corr2d_version", "corr2d_set_profiling",
     "corr2d_get_timings", "corr2d_compute_noalloc", "corr2d_preprocess_perturbation",
-    "corr2d_compute_rows",
+    "corr2d_compute_rows", "corr2d_compute_reduced",
 )
 
 
@@ -88,6 +88,9 @@ def load(path: str | None = None):
             "corr2d_preprocess_perturbation": (i, [vp, i, i, vp, vp, i, i, vp]),
             "corr2d_compute_rows": (i, [vp, i, i, vp, i, i, vp, i, ctypes.POINTER(corr2d_params),
                                         i, i, vp, vp, ctypes.c_long]),
+            "corr2d_compute_reduced": (i, [vp, i, i, vp, i, i, vp, i,
+                                           ctypes.POINTER(corr2d_params), i, vp, vp,
+                                           ctypes.c_long]),
             "corr2d_compute": (i, [vp, i, i, vp, i, i, vp, i, ctypes.POINTER(corr2d_params), vp,
                                    vp, ctypes.c_long, vp, vp]),
             "corr2d_compute_host": (i, [vp, i, i, vp, i, vp, ctypes.POINTER(corr2d_params), vp,
@@ -167,6 +170,13 @@ def corr2d_compute_rows(ctx, m, n1, y1, ld1, n2, y2, ld2, params, row_begin, row
     pp = ctypes.byref(params) if params is not None else None
     _check(ctx, load().corr2d_compute_rows(ctx, m, n1, y1, ld1, n2, y2, ld2, pp, row_begin,
                                            row_count, phi, psi, ldo))
+
+
+def corr2d_compute_reduced(ctx, m, n1, y1, ld1, n2, y2, ld2, params, reduce, phi_r, psi_r,
+                           ldr) -> None:
+    pp = ctypes.byref(params) if params is not None else None
+    _check(ctx, load().corr2d_compute_reduced(ctx, m, n1, y1, ld1, n2, y2, ld2, pp, reduce,
+                                              phi_r, psi_r, ldr))
 
 
 def shard_rows(n1: int, world: int, rank: int, tile: int = 128):
@@ -344,6 +354,18 @@ class Context:
                                      phi.stride(0)))
         corr2d_batch(self.handle, ps, make_params(precision, alpha, norm, None, None, no_mirror,
                                                   hilbert=hilbert))
+
+    def compute_reduced(self, y1, y2, reduce, precision="split", alpha=0.0, norm=0.0,
+                        hilbert=False, ref1=None, ref2=None):
+        """Every reduce-th row and column of Phi and Psi (plot_corr2din3d's `reduce`)."""
+        m, n1 = y1.shape
+        n2 = n1 if y2 is None else y2.shape[1]
+        phi, psi, ldr = self.alloc_out(n1 // reduce, n2 // reduce, y1.device)
+        params = make_params(precision, alpha, norm, ref1, ref2, hilbert=hilbert)
+        corr2d_compute_reduced(self.handle, m, n1, _ptr(y1), y1.stride(0), n2, _ptr(y2),
+                               y2.stride(0) if y2 is not None else 0, params, reduce, _ptr(phi),
+                               _ptr(psi), ldr)
+        return phi[:, :n2 // reduce], psi[:, :n2 // reduce]
 
     def compute_rows(self, y1, y2, row_begin, row_count, precision="split", alpha=0.0, norm=0.0,
                      hilbert=False):

@@ -353,7 +353,8 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
                          float* psi, long ldo, int out_rows, float* sig1, float* sig2,
                          const TileChoice& tc, int ti_begin, int ti_end, int out_row_tile0,
                          bool skip_prep, DevBuf& opsbuf, DevBuf& descbuf,
-                         std::vector<uint8_t>& desc_last, LaunchPlan* cache = nullptr) {
+                         std::vector<uint8_t>& desc_last, LaunchPlan* cache = nullptr,
+                         int cstride = 1) {
   const bool homo = (y2 == nullptr);
   const bool hilbert = (p.flags & CORR2D_FLAG_HILBERT) != 0;
   TcPlan pl = plan_tc(m, n1, n2, homo, p.precision, hilbert);
@@ -392,7 +393,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
     const void* ptrs[] = {y1, y2, phi, psi, sig1, sig2, p.ref1, p.ref2, opsbuf.p, descbuf.p};
     const int ints[] = {m, n1, ld1, n2, ld2, out_rows, p.ref_mode, p.precision, (int)p.flags,
                         tc.bn, tc.mirror, tc.group, ti_begin, ti_end, out_row_tile0,
-                        skip_prep ? 1 : 0};
+                        skip_prep ? 1 : 0, cstride};
     put(ptrs, sizeof ptrs);
     put(ints, sizeof ints);
     put(&ldo, sizeof ldo);
@@ -414,6 +415,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
     j.y = y; j.ref = ref; j.outA = a; j.outB = b; j.scale = sc; j.sigma_out = sig;
     j.wtab = table; j.ld = ld; j.m = m; j.n = n; j.kp = pl.kp; j.jchunks = (m + 63) / 64;
     j.rowlen = pl.rowlen; j.alpha = p.alpha; j.plain_weights = hilbert ? 1 : 0;
+    j.cstride_m1 = cstride - 1;
     int id = (int)jobs.size();
     jobs.push_back(j);
     for (int t = 0; t < (n + PREP_ROWS - 1) / PREP_ROWS; ++t) pitems.push_back(PrepItem{id, t});
@@ -883,6 +885,43 @@ corr2d_status corr2d_compute(corr2d_ctx* ctx, int m, int n1, const float* y1, in
     CUDA_TRY(ctx, cudaMemcpyAsync(sigma2_out, sigma1_out, (size_t)n1 * 4, cudaMemcpyDeviceToDevice, ctx->stream));
   else if (homo && sigma2_out)
     return fail(ctx, CORR2D_EINVAL, "homo correlation: pass sigma1_out to get sigma2_out");
+  ctx->err.clear();
+  return CORR2D_OK;
+}
+
+corr2d_status corr2d_compute_reduced(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1,
+                                     int n2, const float* y2, int ld2,
+                                     const corr2d_params* params, int reduce, float* phi_r,
+                                     float* psi_r, long ldr) {
+  if (!ctx) return CORR2D_EINVAL;
+  corr2d_params p;
+  if (params) p = *params; else corr2d_params_default(&p);
+  const bool homo = (y2 == nullptr);
+  if (homo) { n2 = n1; ld2 = ld1; }
+  if (reduce < 1 || reduce > n1 || reduce > n2)
+    return fail(ctx, CORR2D_EINVAL, "reduce = %d must be in [1, min(n1, n2)]", reduce);
+  const int n1r = n1 / reduce, n2r = n2 / reduce;
+  DeviceGuard g(ctx->device);
+  corr2d_status st = validate_compute(ctx, m, n1, y1, ld1, n2, homo ? nullptr : y2, ld2, p, phi_r,
+                                      psi_r, ldr < n2 ? n2 : ldr, true);
+  if (st != CORR2D_OK) return st;
+  if (ldr < n2r || ldr % 4 != 0)
+    return fail(ctx, CORR2D_EINVAL, "ldr must be >= n2 / reduce and a multiple of 4");
+  if (p.precision == CORR2D_PREC_FP32)
+    return fail(ctx, CORR2D_EUNSUPPORTED, "the reduced map runs the tensor-core precisions");
+  if (p.ref_mode == CORR2D_REF_USER) {  // the references are sampled like the stacks
+    p.ref1 = p.ref1 + (reduce - 1);
+    if (!homo) p.ref2 = p.ref2 + (reduce - 1);
+  }
+  // variables nu = reduce (i + 1) - 1: the stacks start at column reduce - 1,
+  // stride reduce
+  const float* y1s = y1 + (reduce - 1);
+  const float* y2s = homo ? nullptr : y2 + (reduce - 1);
+  TileChoice tc{128, homo ? 1 : 0, 0};
+  st = enqueue_tc(ctx, m, n1r, y1s, ld1, n2r, y2s, ld2, p, phi_r, psi_r, ldr, n1r, nullptr,
+                  nullptr, tc, 0, (n1r + TILE_M - 1) / TILE_M, 0, false, ctx->ops, ctx->desc,
+                  ctx->desc_host, nullptr, reduce);
+  if (st != CORR2D_OK) return st;
   ctx->err.clear();
   return CORR2D_OK;
 }

@@ -71,6 +71,9 @@ struct PrepJob {
   int rowlen;              // operand row length in elements
   int plain_weights;       // 1: outB gets weight 1 everywhere (Hilbert variant);
                            // 0: the half-spectrum weights 1 (omega = 0) / 2
+  int cstride_m1;          // column stride of y (and ref) minus 1: variable nu is
+                           // column nu * (cstride_m1 + 1) (decimated preview)
+  int pad2_;
   double alpha;
 };
 

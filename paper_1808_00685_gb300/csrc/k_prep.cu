@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
   }
   // ---- 1. FP64 partial sums over steps j = g, g+4, ..., FP32 extremes
   const float* y = job.y;
+  const long col = (long)nu * (job.cstride_m1 + 1);  // column of variable nu in y
   const long ld = job.ld;
   {
     double s = 0.0;
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
     if (valid) {
       if (job.ref) {
         for (int j = g; j < m; j += PREP_GROUPS) {
-          const float v = y[(long)j * ld + nu];
+          const float v = y[(long)j * ld + col];
           mn = fminf(mn, v);
           mx = fmaxf(mx, v);
         }
@@ -176,10 +177,10 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
         float res = 0.f;
         int j = g;
         for (; j + 3 * PREP_GROUPS < m; j += 4 * PREP_GROUPS) {
-          const float a = y[(long)j * ld + nu];
-          const float b = y[(long)(j + PREP_GROUPS) * ld + nu];
-          const float c = y[(long)(j + 2 * PREP_GROUPS) * ld + nu];
-          const float d = y[(long)(j + 3 * PREP_GROUPS) * ld + nu];
+          const float a = y[(long)j * ld + col];
+          const float b = y[(long)(j + PREP_GROUPS) * ld + col];
+          const float c = y[(long)(j + 2 * PREP_GROUPS) * ld + col];
+          const float d = y[(long)(j + 3 * PREP_GROUPS) * ld + col];
           float s1, e1, s2, e2, s4, e3;
           two_sum(a, b, s1, e1);
           two_sum(c, d, s2, e2);
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
           mx = fmaxf(fmaxf(mx, fmaxf(a, b)), fmaxf(c, d));
         }
         for (; j < m; j += PREP_GROUPS) {
-          const float v = y[(long)j * ld + nu];
+          const float v = y[(long)j * ld + col];
           s += (double)v;
           mn = fminf(mn, v);
           mx = fmaxf(mx, v);
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
         mn = fminf(mn, red_mn[k * PREP_ROWS + r]);
         mx = fmaxf(mx, red_mx[k * PREP_ROWS + r]);
       }
-      ref = job.ref ? (double)job.ref[nu] : s / (double)m;
+      ref = job.ref ? (double)job.ref[col] : s / (double)m;
       amax = fmax((double)mx - ref, ref - (double)mn);  // extremes of |y - ref|
     }
     int ey = 0;
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
       for (int e = 0; e < 8; ++e) {
         const int j = kc * 64 + jg * 8 + e;
         // FP64 centering, rounded once to FP32; scaling by 2^ey is exact
-        const float d = (valid && j < m) ? (float)((double)y[(long)j * ld + nu] - ref) : 0.f;
+        const float d = (valid && j < m) ? (float)((double)y[(long)j * ld + col] - ref) : 0.f;
         const float sq = fmaf(d, d, -ss_c);
         const float tsum = ss + sq;
         ss_c = (tsum - ss) - sq;

@@ -375,3 +375,23 @@ def test_upper_triangle_output(ctx):
     r, c = np.indices((n, n))
     far_lower = (r // 32) > (c // 32)
     assert np.all(np.isnan(ph[far_lower])) and np.all(np.isnan(ps[far_lower]))
+
+
+@pytest.mark.parametrize("reduce", [2, 5, 32])
+def test_reduced_map_matches_the_full_map(ctx, reduce):
+    """Sec. 4.3 `reduce`: only every reduce-th variable is correlated; equals the
+    decimated full result (oracle) including the per-variable reference and scaling."""
+    y1 = workloads.random_stack(30, 640, seed=24, offset=2.0)
+    y2 = workloads.random_stack(30, 300, seed=25, offset=-1.0)
+    for a, b in ((y1, None), (y1, y2)):
+        phr, psr = ctx.compute_reduced(dev(a), None if b is None else dev(b), reduce, alpha=0.5)
+        ctx.synchronize()
+        ophi, opsi, _, _ = oracle.corr2d(a, b, alpha=0.5)
+        check(host(phr), host(psr), oracle.reduce_map(ophi, reduce),
+              oracle.reduce_map(opsi, reduce), 1e-5, f"reduce={reduce}")
+    r1 = y1[0].copy()
+    phr, psr = ctx.compute_reduced(dev(y1), None, reduce, ref1=dev(r1))
+    ctx.synchronize()
+    ophi, opsi, _, _ = oracle.corr2d(y1, ref1=r1)
+    check(host(phr), host(psr), oracle.reduce_map(ophi, reduce), oracle.reduce_map(opsi, reduce),
+          1e-5, f"reduce={reduce} user ref")

@@ -425,6 +425,13 @@ def test_perturbation_interp_identity_and_linear_signal():
         oracle.interp_perturbation(np.array([0.0, 1.0, 1.0]), np.zeros((3, 2), np.float32), 4)
 
 
+@pytest.mark.parametrize("reduce", [1, 2, 3, 7])
+def test_reduce_map_is_decimation(reduce):
+    """Sec. 4.3 `reduce`: 1-based indices divisible by reduce == numpy slicing from reduce-1."""
+    M = np.arange(23 * 17, dtype=np.float64).reshape(23, 17)
+    assert np.array_equal(oracle.reduce_map(M, reduce), M[reduce - 1::reduce, reduce - 1::reduce])
+
+
 def test_interp_rejects_non_increasing_axis():
     x = np.array([0.0, 1.0, 1.0, 2.0])
     with pytest.raises(ValueError):
