@@ -5,11 +5,15 @@
 // Tensor-core kernel (k_prep_tc): one CTA of 256 threads per 128 spectral
 // variables (two CTAs per SM); two threads share a variable's perturbation
 // steps.
-//   1. FP64 reference (perturbation mean or the caller's spectrum) from FP64
-//      partial sums; FP32 extremes of y give the range of y - ref.
-//   2. FP64 centering y - ref, rounded once to FP32, scaled by a power of two
-//      and split into 16-bit planes (FP16 hi/lo, or one BF16 plane), written
-//      to shared memory as the A operand (variables x steps, K-major,
+//   1. Reference (perturbation mean or the caller's spectrum) as a
+//      double-float pair rh + rl: the sum of y is accumulated with TwoSum
+//      into a (hi, lo) FP32 pair (each addition adds an error of order
+//      2^-47 of the running sum), then divided by m with an exact remainder.
+//      FP32 extremes of y give the range of y - ref.
+//   2. Centering y - rh - rl with TwoSum (the result is y - ref rounded once
+//      to FP32, up to a rounding of the 2^-48-sized tail), scaled by a power
+//      of two and split into 16-bit planes (FP16 hi/lo, or one BF16 plane),
+//      written to shared memory as the A operand (variables x steps, K-major,
 //      128-byte swizzle), 64 steps at a time; compensated FP32 sum of squares.
 //   3. tcgen05.mma contracts them with the twiddle matrix W (rows: cos and
 //      -sin of 2 pi ((omega j) mod m) / m, FP64-built, split likewise) into
@@ -18,8 +22,10 @@
 //   4. Epilogue (8 warps, two per TMEM lane quadrant): row maximum,
 //      power-of-two rescale, split into planes, operand rows (unweighted for
 //      stack 1, weight w = 1 / 2 for stack 2), scale sigma^-alpha 2^-E, sigma.
-// FP64 is kept to the mean and the centering subtraction: GB300's FP64 rate is
-// low, so the range comes from FP32 min/max and the sum of squares from FP32.
+// No FP64 arithmetic runs per element: GB300's FP64 pipe retires about one
+// operation per clock per SM, so the FP64 conversions and subtraction of a
+// plain FP64 centering bound the kernel; double-float FP32 arithmetic gives
+// the same FP32 results at the FP32 rate.
 #include <cmath>
 #include "internal.h"
 #include "ptx.cuh"
@@ -29,9 +35,9 @@ namespace c2d {
 constexpr int PREP_THREADS = 256;
 constexpr int PREP_GROUPS = PREP_THREADS / PREP_ROWS;  // threads per variable (2)
 constexpr int PREP_JG = 8 / PREP_GROUPS;               // 8-step groups per thread per chunk
-// reduction scratch: FP64 sums (4 x 128), FP32 min / max / sum of squares
-// (3 x 4 x 128; the min slots are reused for the epilogue row maxima), per-row
-// exponent (128 ints) and reference (128 doubles)
+// reduction scratch: double-float sums (2 x 2 x 128 floats), FP32 min / max /
+// sum of squares (3 x 2 x 128; the min slots are reused for the epilogue row
+// maxima), per-row exponent (128 ints) and double-float reference (128 pairs)
 constexpr int PREP_SCRATCH = PREP_GROUPS * PREP_ROWS * (8 + 4 + 4 + 4) + PREP_ROWS * (4 + 8);
 
 // Error-free sum of two floats: a + b = s + e exactly (Knuth's TwoSum).
@@ -39,6 +45,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   const float bb = s - a;
   e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) += x + r, with x exact and r a small correction: TwoSum of hi and
+// x, the low parts added to its error, renormalised by TwoSum.
+__device__ __forceinline__ void df_acc(float& hi, float& lo, float x, float r) {
+  float s, e;
+  two_sum(hi, x, s, e);
+  e += lo + r;
+  two_sum(s, e, hi, lo);
 }
 
 // 16 consecutive TMEM columns of this warp's lanes.
@@ -134,12 +149,13 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
   uint8_t* sA = base;
   uint8_t* sW = base + P * PREP_ROWS * 128;
   const uint32_t wbytes = (uint32_t)ncomp * 128u;
-  double* red_s = (double*)(sW + P * wbytes);              // [4][128] partial sums
-  float* red_mn = (float*)(red_s + PREP_GROUPS * PREP_ROWS);
+  float* red_sh = (float*)(sW + P * wbytes);               // [2][128] sums, high parts
+  float* red_sl = red_sh + PREP_GROUPS * PREP_ROWS;        // [2][128] sums, low parts
+  float* red_mn = red_sl + PREP_GROUPS * PREP_ROWS;
   float* red_mx = red_mn + PREP_GROUPS * PREP_ROWS;
   float* red_ss = red_mx + PREP_GROUPS * PREP_ROWS;        // Kahan partials
   float* red_max = red_mn;                                 // epilogue row maxima (reuse)
-  double* row_ref = (double*)(red_ss + PREP_GROUPS * PREP_ROWS);
+  float2* row_ref = (float2*)(red_ss + PREP_GROUPS * PREP_ROWS);  // (rh, rl)
   int* row_ey = (int*)(row_ref + PREP_ROWS);
   uint64_t* bars = (uint64_t*)(row_ey + PREP_ROWS);
   uint32_t* tmem_slot = (uint32_t*)(bars + 2);
@@ -155,12 +171,12 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
     tmem_alloc(smem_u32(tmem_slot), ncols);
     tmem_relinquish();
   }
-  // ---- 1. FP64 partial sums over steps j = g, g+4, ..., FP32 extremes
+  // ---- 1. double-float partial sums over steps j = g, g+2, ..., FP32 extremes
   const float* y = job.y;
   const long col = (long)nu * (job.cstride_m1 + 1);  // column of variable nu in y
   const long ld = job.ld;
   {
-    double s = 0.0;
+    float sh = 0.f, sl = 0.f;
     float mn = __int_as_float(0x7f800000), mx = -__int_as_float(0x7f800000);
     if (valid) {
       if (job.ref) {
@@ -170,36 +186,37 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
           mx = fmaxf(mx, v);
         }
       } else {
-        // FP64 accumulation of error-free FP32 partial sums: four values are
-        // summed exactly as s4 + e4 by TwoSum, s4 goes into the FP64 sum, the
-        // residuals e4 (each below half an ulp of s4) into a FP32 sum that
-        // joins the FP64 sum at the end.  One FP64 add per four values.
-        float res = 0.f;
+        // Sixteen loads are in flight before the first is used.  Each four
+        // values are summed exactly as s4 + (e1 + e2 + e3) by TwoSum (the
+        // residuals are below half an ulp of s4, their FP32 sum is off by
+        // ~2^-48 s4); the pair joins the running (sh, sl) sum.
         int j = g;
-        for (; j + 3 * PREP_GROUPS < m; j += 4 * PREP_GROUPS) {
-          const float a = y[(long)j * ld + col];
-          const float b = y[(long)(j + PREP_GROUPS) * ld + col];
-          const float c = y[(long)(j + 2 * PREP_GROUPS) * ld + col];
-          const float d = y[(long)(j + 3 * PREP_GROUPS) * ld + col];
-          float s1, e1, s2, e2, s4, e3;
-          two_sum(a, b, s1, e1);
-          two_sum(c, d, s2, e2);
-          two_sum(s1, s2, s4, e3);
-          s += (double)s4;
-          res += (e1 + e2) + e3;
-          mn = fminf(fminf(mn, fminf(a, b)), fminf(c, d));
-          mx = fmaxf(fmaxf(mx, fmaxf(a, b)), fmaxf(c, d));
+        for (; j + 15 * PREP_GROUPS < m; j += 16 * PREP_GROUPS) {
+          float v[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] = __ldg(y + (long)(j + e * PREP_GROUPS) * ld + col);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float a = v[4 * q], b = v[4 * q + 1], c = v[4 * q + 2], d = v[4 * q + 3];
+            float s1, e1, s2, e2, s4, e3;
+            two_sum(a, b, s1, e1);
+            two_sum(c, d, s2, e2);
+            two_sum(s1, s2, s4, e3);
+            df_acc(sh, sl, s4, (e1 + e2) + e3);
+            mn = fminf(fminf(mn, fminf(a, b)), fminf(c, d));
+            mx = fmaxf(fmaxf(mx, fmaxf(a, b)), fmaxf(c, d));
+          }
         }
         for (; j < m; j += PREP_GROUPS) {
           const float v = y[(long)j * ld + col];
-          s += (double)v;
+          df_acc(sh, sl, v, 0.f);
           mn = fminf(mn, v);
           mx = fmaxf(mx, v);
         }
-        s += (double)res;
       }
     }
-    red_s[g * PREP_ROWS + r] = s;
+    red_sh[g * PREP_ROWS + r] = sh;
+    red_sl[g * PREP_ROWS + r] = sl;
     red_mn[g * PREP_ROWS + r] = mn;
     red_mx[g * PREP_ROWS + r] = mx;
   }
@@ -207,31 +224,40 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
   __syncthreads();
   tc_fence_after();
   if (g == 0) {
-    double ref = 0.0, amax = 0.0;
+    float rh = 0.f, rl = 0.f, amax = 0.f;
     if (valid) {
       float mn = red_mn[r], mx = red_mx[r];
-      double s = red_s[r];
+      float sh = red_sh[r], sl = red_sl[r];
       for (int k = 1; k < PREP_GROUPS; ++k) {
-        s += red_s[k * PREP_ROWS + r];
+        df_acc(sh, sl, red_sh[k * PREP_ROWS + r], red_sl[k * PREP_ROWS + r]);
         mn = fminf(mn, red_mn[k * PREP_ROWS + r]);
         mx = fmaxf(mx, red_mx[k * PREP_ROWS + r]);
       }
-      ref = job.ref ? (double)job.ref[col] : s / (double)m;
-      amax = fmax((double)mx - ref, ref - (double)mn);  // extremes of |y - ref|
+      if (job.ref) {
+        rh = job.ref[col];
+      } else {
+        // (sh + sl) / m: the remainder sh - q1 m of the rounded quotient q1 is
+        // exact in FP32 and is computed exactly by the FMA
+        const float fm = (float)m;
+        const float q1 = __fdiv_rn(sh, fm);
+        const float q2 = __fdiv_rn(fmaf(-q1, fm, sh) + sl, fm);
+        two_sum(q1, q2, rh, rl);
+      }
+      amax = fmaxf((mx - rh) - rl, (rh - mn) + rl);  // extremes of |y - ref|
     }
     int ey = 0;
-    if (amax > 0.0) {
+    if (amax > 0.f) {
       int e;
-      frexp(amax, &e);  // amax < 2^e
+      frexpf(amax, &e);  // amax < 2^e
       ey = 14 - e;      // scaled maximum in [2^13, 2^14)
       if (ey > 126) ey = 126;  // keep 2^ey a normal FP32 number (data below ~1e-34)
     }
-    row_ref[r] = ref;
+    row_ref[r] = make_float2(rh, rl);
     row_ey[r] = ey;
   }
   __syncthreads();
   const uint32_t tmem = *tmem_slot;
-  const double ref = row_ref[r];
+  const float2 ref = row_ref[r];
   const float fy = ldexpf(1.0f, row_ey[r]);
   float ss = 0.f, ss_c = 0.f;  // Kahan sum of (y - ref)^2 over this thread's steps
   bool ok = true;
@@ -244,6 +270,16 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
   const uint32_t id1 = idesc_f16(128, ncomp - 256 > 0 ? ncomp - 256 : 16, P == 1, false);
   int w_armed = 0, m_committed = 0;  // thread 0: async operations started
   for (int kc = 0; kc < jchunks; ++kc) {
+    // this thread's groups of 8 steps: jg = g, g + 2, g + 4, g + 6; the loads
+    // are issued before waiting for the previous chunk's MMAs
+    float yv[PREP_JG][8];
+#pragma unroll
+    for (int h = 0; h < PREP_JG; ++h)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int j = kc * 64 + (g + PREP_GROUPS * h) * 8 + e;
+        yv[h][e] = (valid && j < m) ? __ldg(y + (long)j * ld + col) : 0.f;
+      }
     if (kc > 0) ok = ok && mbar_wait(mbar, (kc - 1) & 1, wc);  // smem free again
     if (t == 0 && ok) {
       mbar_arrive_expect_tx(wbar, P * wbytes);
@@ -252,7 +288,6 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
         bulk_load(smem_u32(sW + p * wbytes), job.wtab + ((size_t)kc * P + p) * wbytes, wbytes,
                   wbar);
     }
-    // this thread's two groups of 8 steps: jg = g and g + 4
 #pragma unroll
     for (int h = 0; h < PREP_JG; ++h) {
       const int jg = g + PREP_GROUPS * h;
@@ -260,8 +295,13 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int j = kc * 64 + jg * 8 + e;
-        // FP64 centering, rounded once to FP32; scaling by 2^ey is exact
-        const float d = (valid && j < m) ? (float)((double)y[(long)j * ld + col] - ref) : 0.f;
+        // centering y - rh - rl; scaling by 2^ey is exact
+        float d = 0.f;
+        if (valid && j < m) {
+          float ds, de;
+          two_sum(yv[h][e], -ref.x, ds, de);
+          d = ds + (de - ref.y);
+        }
         const float sq = fmaf(d, d, -ss_c);
         const float tsum = ss + sq;
         ss_c = (tsum - ss) - sq;
@@ -367,16 +407,33 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
     }
   }
   if (part == 0 && valid_e) {
-    double s2sum = 0.0;
-    for (int k = 0; k < PREP_GROUPS; ++k) s2sum += (double)red_ss[k * PREP_ROWS + lr];
-    const double sigma = sqrt(s2sum / (double)(m - 1));
-    double sc;
-    if (job.alpha > 0.0)
-      sc = (sigma == 0.0) ? 0.0 : pow(sigma, -job.alpha);
-    else
-      sc = 1.0;
-    job.scale[nu_e] = (float)ldexp(sc, -(row_ey[lr] + eY));
-    if (job.sigma_out) job.sigma_out[nu_e] = (float)sigma;
+    float s2sum = red_ss[lr];
+    for (int k = 1; k < PREP_GROUPS; ++k) s2sum += red_ss[k * PREP_ROWS + lr];
+    const float sigma = sqrtf(__fdiv_rn(s2sum, (float)(m - 1)));
+    float sc = 1.f;
+    int ex = 0;
+    if (job.alpha > 0.0) {
+      if (sigma == 0.f) {
+        sc = 0.f;
+      } else if (job.alpha <= 64.0) {
+        // sigma^-alpha = f^-alpha 2^(-alpha k) with sigma = f 2^k, f in
+        // [0.5, 1): f^-alpha <= 2^64 cannot overflow, and -alpha k is split
+        // into integer and fraction in FP64 (two operations per variable)
+        int k;
+        const float f = frexpf(sigma, &k);
+        const double tk = fmin(fmax(-job.alpha * (double)k, -1024.0), 1024.0);
+        const double ti = floor(tk);
+        sc = powf(f, (float)-job.alpha) * exp2f((float)(tk - ti));
+        ex = (int)ti;
+      } else {
+        const double p = pow((double)sigma, -job.alpha);
+        int k;
+        sc = (float)frexp(p, &k);
+        ex = k;
+      }
+    }
+    job.scale[nu_e] = ldexpf(sc, ex - (row_ey[lr] + eY));
+    if (job.sigma_out) job.sigma_out[nu_e] = sigma;
   }
   if (t == 0 && !ok) {  // abort: let started copies and MMAs finish
     if (w_armed > 0) mbar_wait_drain(wbar, (w_armed - 1) & 1, limit_ns);

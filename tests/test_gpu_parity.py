@@ -68,7 +68,7 @@ def test_c1_small_homo(ctx, prec):
 
 @pytest.mark.parametrize("prec", ["split", "fp32"])
 def test_c2_homo_offset_baseline(ctx, prec):
-    """m=64, n=4096, baseline offset 10: FP64 centering on the GPU."""
+    """m=64, n=4096, baseline offset 10: centering cancels the baseline."""
     y = workloads.c2()
     phi, psi = run(ctx, y, precision=prec)
     ophi, opsi, _, _ = oracle.corr2d(y, nthreads=oracle.max_threads())
@@ -80,6 +80,30 @@ def test_c2_homo_offset_baseline(ctx, prec):
     check(phi, psi, ophi, opsi, TOL[prec], f"c2 {prec} exact symmetry")
     assert np.array_equal(phi, phi.T) and np.array_equal(psi, -psi.T)
     assert np.all(np.diag(psi) == 0)
+
+
+@pytest.mark.parametrize("m", [512, 257])
+def test_large_baseline_small_dynamic_part(ctx, m):
+    """Baseline 1000 (stack 2: -3000) under a dynamic part of 0.01: the mean
+    must hold ~20 significant bits below the baseline's ulp for the centred
+    spectra to keep theirs; sigma and sigma^-alpha at alpha = 0.5, 1, 3."""
+    import paper_1808_00685_gb300 as pkg
+    n1, n2 = 700, 333
+    y1 = workloads.random_stack(m, n1, seed=m + 1, offset=1000.0, scale=0.01)
+    y2 = workloads.random_stack(m, n2, seed=m + 2, offset=-3000.0, scale=0.01)
+    phi, psi = run(ctx, y1, precision="split")
+    ophi, opsi, os1, _ = oracle.corr2d(y1, nthreads=oracle.max_threads())
+    check(phi, psi, ophi, opsi, 1e-5, f"m={m} homo")
+    for alpha in (0.5, 1.0, 3.0):
+        d1, d2 = dev(y1), dev(y2)
+        p, q, lo = pkg.Context.alloc_out(n1, n2, d1.device)
+        ph, ps, s1, s2 = ctx.compute(d1, d2, out=(p, q), precision="split", alpha=alpha,
+                                     want_sigma=True)
+        ctx.synchronize()
+        ophi, opsi, os1, os2 = oracle.corr2d(y1, y2, alpha=alpha, nthreads=oracle.max_threads())
+        check(host(ph)[:, :n2], host(ps)[:, :n2], ophi, opsi, 1e-5, f"m={m} alpha={alpha}")
+        assert np.allclose(s1.cpu().numpy(), os1, rtol=1e-6)
+        assert np.allclose(s2.cpu().numpy(), os2, rtol=1e-6)
 
 
 def test_c3_hetero_with_preprocessing(ctx):
