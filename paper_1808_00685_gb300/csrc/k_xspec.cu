@@ -16,7 +16,10 @@
 //               for Psi): TMEM -> registers, scale, 128-byte-swizzled staging
 //               box, TMA store of 32x32 FP32 boxes.  For homo problems the
 //               mirrored box is stored too (Phi symmetric, Psi antisymmetric),
-//               so only tiles with ti <= tj are computed.
+//               so only tiles with ti <= tj are computed.  Each warp stages
+//               its boxes in a ring of XS_EPI_SLOTS slots, one bulk group per
+//               box, and waits only for the group that last read the slot it
+//               is about to overwrite.
 // TMEM holds two accumulator sets (2 x 256 columns): the MMAs of tile i+1
 // run while the epilogue of tile i streams its stores.
 #include "internal.h"
@@ -28,7 +31,8 @@ constexpr int XS_STAGES = 4;
 constexpr int XS_STAGE_BYTES = 2 * TILE_M * 128;  // A chunk + B chunk (bn <= 128 rows)
 constexpr int XS_EPI_WARPS = 8;
 constexpr int XS_BOX_BYTES = 32 * 32 * 4;
-constexpr int XS_EPI_SLOTS = 2;                   // staging boxes per epilogue warp
+constexpr int XS_EPI_SLOTS = 2;                   // staging boxes per epilogue warp (ring)
+static_assert(XS_EPI_SLOTS >= 2, "a box and its mirror need two staging slots");
 constexpr int XS_THREADS = 64 + 32 * XS_EPI_WARPS;
 constexpr size_t XS_SMEM = 1024 + (size_t)XS_STAGES * XS_STAGE_BYTES +
                            (size_t)XS_EPI_WARPS * XS_EPI_SLOTS * XS_BOX_BYTES +
@@ -214,11 +218,10 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
     const int q = warp & 3;       // TMEM lane quadrant this warp may access
     const float sg = half ? -1.f : 1.f;
     const uint64_t stream_out = l2_policy_evict_first();  // written once, never re-read here
-    uint8_t* slot0 = epi + ew * XS_EPI_SLOTS * XS_BOX_BYTES;
-    uint8_t* slot1 = slot0 + XS_BOX_BYTES;
+    uint8_t* ring = epi + ew * XS_EPI_SLOTS * XS_BOX_BYTES;
     float* s2w = s2stage + ew * TILE_N;
     int lt = 0;
-    bool pending = false;  // lane 0 has a bulk group whose smem reads may be in flight
+    int slot = 0;  // next slot of this warp's staging ring
     int cur_prob = -1;
     const CUtensorMap* tm = nullptr;
     const float* s1p = nullptr;
@@ -293,9 +296,19 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
           v[i + 2] = v[i + 2] * rs * s4.z;
           v[i + 3] = v[i + 3] * rs * s4.w;
         }
-        // the previous group's reads of both slots must be complete
-        if (pending && lane == 0) bulk_wait_read<0>();
+        // The slots about to be written were last read by the group committed
+        // XS_EPI_SLOTS (second slot: XS_EPI_SLOTS - 1) groups ago; lane 0
+        // committed them, so lane 0 waits.
+        const bool two = mirror && !tri;
+        if (lane == 0) {
+          if (two)
+            bulk_wait_read<XS_EPI_SLOTS - 2>();
+          else
+            bulk_wait_read<XS_EPI_SLOTS - 1>();
+        }
         __syncwarp();
+        uint8_t* slot0 = ring + slot * XS_BOX_BYTES;
+        uint8_t* slot1 = ring + ((slot + 1) % XS_EPI_SLOTS) * XS_BOX_BYTES;
         if (!tri) {
           // box (rows row0.., cols col0..): row = lane, 8 swizzled 16-byte chunks
 #pragma unroll
@@ -324,10 +337,13 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
         __syncwarp();
         if (lane == 0) {
           tma_store_2d_hint(tm, col0, row0 - orow_off, smem_u32(slot0), stream_out);
-          if (mirror && !tri) tma_store_2d_hint(tm, row0, col0, smem_u32(slot1), stream_out);
           bulk_commit();
+          if (two) {
+            tma_store_2d_hint(tm, row0, col0, smem_u32(slot1), stream_out);
+            bulk_commit();
+          }
         }
-        pending = true;
+        slot = (slot + (two ? 2 : 1)) % XS_EPI_SLOTS;
       }
       // this tile's accumulators are consumed: hand the TMEM buffer back
       tc_fence_before();
