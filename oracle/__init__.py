@@ -84,6 +84,9 @@ def _configure(lib):
     lib.oracle_interp_perturbation.restype = ctypes.c_int
     lib.oracle_interp_perturbation.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _fp,
                                                ctypes.c_long, ctypes.c_int, _dp]
+    lib.oracle_interp_spline.restype = ctypes.c_int
+    lib.oracle_interp_spline.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _fp, ctypes.c_long,
+                                         ctypes.c_int, _dp]
     lib.oracle_max_threads.restype = ctypes.c_int
     return lib
 
@@ -287,16 +290,20 @@ def interp_linear(x_raw: np.ndarray, y_raw: np.ndarray, n_out: int, ref=None):
     return out, dyn
 
 
-def interp_perturbation(time: np.ndarray, y: np.ndarray, N: int) -> np.ndarray:
-    """Linear resampling along the perturbation axis onto N equidistant values
-    (Sec. 4.2 interpolation snippet, reading R13).  y is m x n; returns N x n FP64."""
+def interp_perturbation(time: np.ndarray, y: np.ndarray, N: int,
+                        method: str = "linear") -> np.ndarray:
+    """Resampling along the perturbation axis onto N equidistant values (Sec. 4.2
+    interpolation snippet, reading R13): method "linear" (approxfun) or "spline"
+    (splinefun's default fmm spline).  y is m x n; returns N x n FP64."""
     time, tp = _f64(time)
     y, yp = _f32(y)
     m, n = y.shape
     out = np.empty((N, n), np.float64)
-    rc = _load().oracle_interp_perturbation(m, n, tp, yp, n, N, out.ctypes.data_as(_dp))
+    fn = {"linear": _load().oracle_interp_perturbation,
+          "spline": _load().oracle_interp_spline}[method]
+    rc = fn(m, n, tp, yp, n, N, out.ctypes.data_as(_dp))
     if rc != 0:
-        raise ValueError("oracle_interp_perturbation rejected its arguments")
+        raise ValueError(f"oracle {method} interpolation rejected its arguments")
     return out
 
 

@@ -11,7 +11,7 @@
  * Everything is plain double arithmetic, straight loops, no blocking, no
  * fusion, no FFT.  Each function names the passage of the paper it follows.
  * Where the paper is silent or inconsistent the reading taken is written next
- * to the code (readings R1..R12, listed again in the design notes):
+ * to the code (readings R1..R13, listed again in the design notes):
  *
  *  R1  Eq. disint2d sums over all m frequencies; for real input that sum is
  *      real (Eq. symmeFT), so the asynchronous part would vanish.  The package
@@ -39,9 +39,13 @@
  *  R12 Spectral-axis preprocessing: linear interpolation onto
  *      x_k = x_0 + k (x_last - x_0)/(n_out - 1), k = 0..n_out-1, last point
  *      set to x_last exactly; x must be strictly increasing.
- *  R13 Perturbation-axis interpolation (Sec. 4.2) with the linear function
- *      (approxfun); the package's default splinefun is not specified further
- *      in the paper and is not stated here.
+ *  R13 Perturbation-axis interpolation (Sec. 4.2): the linear function
+ *      (approxfun) and the package's default, splinefun, read as R's default
+ *      spline method "fmm" (Forsythe, Malcolm and Moler, 1977): the C^2
+ *      interpolating cubic spline whose third derivative on the first and
+ *      last interval equals that of the cubic through the first and last four
+ *      points; with three points those third derivatives are taken as 0 (the
+ *      interpolating parabola), with two points the spline is the line.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -289,8 +293,8 @@ int oracle_interp_linear(int m, int n_raw, const double* x_raw, const float* y_r
  * length.out = N), i.e. T_k = t_0 + k (t_last - t_0)/(N - 1) with the last
  * value t_last exactly, then every spectral variable (column nu of the m x n
  * matrix) is evaluated at the T_k through an interpolating function of its
- * values over Time.  The package offers approxfun (linear) and splinefun; the
- * linear function is the one stated here (reading R13).  Time must be
+ * values over Time.  The package offers approxfun (linear) and splinefun; this
+ * is the linear function (reading R13; the spline is oracle_interp_spline).  Time must be
  * strictly increasing.  Output: N x n row-major.  Returns 0, or 1 on invalid
  * arguments.
  */
@@ -313,6 +317,98 @@ int oracle_interp_perturbation(int m, int n, const double* time, const float* y,
       out[(long)k * n + v] = ya + u * (yb - ya);
     }
   }
+  return 0;
+}
+
+/*
+ * Perturbation-axis interpolation through the default interpolating function
+ * of the package, splinefun (Sec. 4.2; reading R13: R's "fmm" spline).  Same
+ * new perturbation values as oracle_interp_perturbation.  For each spectral
+ * variable the spline s is cubic on every [t_i, t_i+1], s(t_i) = y_i, and s is
+ * twice continuously differentiable.  With M_i = s''(t_i), h_i = t_i+1 - t_i
+ * and D_i = (y_i+1 - y_i)/h_i the continuity of s' at the inner knots gives
+ *   h_i-1 M_i-1 + 2 (h_i-1 + h_i) M_i + h_i M_i+1 = 6 (D_i - D_i-1),
+ * i = 1..m-2, and the end conditions fix the third derivative of s on the
+ * first and last interval:
+ *   (M_1 - M_0) / h_0 = 6 f[t_0, t_1, t_2, t_3],
+ *   (M_m-1 - M_m-2) / h_m-2 = 6 f[t_m-4, ..., t_m-1]
+ * (f[...] the divided differences: 6 f[four points] is the third derivative
+ * of the cubic through them); with m = 3 both are 0, with m = 2 M = 0.  The
+ * tridiagonal system is solved by Gaussian elimination in knot order, then
+ *   s(T) = (M_s A^3 + M_s+1 B^3) / (6 h) + (y_s - M_s h^2/6) A / h
+ *        + (y_s+1 - M_s+1 h^2/6) B / h,   A = t_s+1 - T, B = T - t_s, h = h_s
+ * on the segment s of T chosen as in the linear case.  Output N x n
+ * row-major; returns 0, or 1 on invalid arguments.
+ */
+static double oracle_third_divided_difference(const double* t, const double* y) {
+  double f01 = (y[1] - y[0]) / (t[1] - t[0]);
+  double f12 = (y[2] - y[1]) / (t[2] - t[1]);
+  double f23 = (y[3] - y[2]) / (t[3] - t[2]);
+  double f012 = (f12 - f01) / (t[2] - t[0]);
+  double f123 = (f23 - f12) / (t[3] - t[1]);
+  return (f123 - f012) / (t[3] - t[0]);
+}
+
+int oracle_interp_spline(int m, int n, const double* time, const float* y, long ld, int N,
+                         double* out) {
+  if (m < 2 || n < 1 || N < 2 || !time || !y || !out || ld < n) return 1;
+  for (int j = 1; j < m; ++j)
+    if (!(time[j] > time[j - 1])) return 1;
+  double* yv = malloc(sizeof(double) * (size_t)m);
+  double* M = malloc(sizeof(double) * (size_t)m);
+  double* sub = malloc(sizeof(double) * (size_t)m);
+  double* dia = malloc(sizeof(double) * (size_t)m);
+  double* sup = malloc(sizeof(double) * (size_t)m);
+  double* rhs = malloc(sizeof(double) * (size_t)m);
+  if (!yv || !M || !sub || !dia || !sup || !rhs) {
+    free(yv); free(M); free(sub); free(dia); free(sup); free(rhs);
+    return 1;
+  }
+  const double t0 = time[0], t1 = time[m - 1];
+  const double step = (t1 - t0) / (double)(N - 1);
+  for (int v = 0; v < n; ++v) {
+    for (int i = 0; i < m; ++i) yv[i] = (double)y[(long)i * ld + v];
+    if (m == 2) {
+      M[0] = M[1] = 0.0;
+    } else {
+      /* rows of the tridiagonal system: sub M_i-1 + dia M_i + sup M_i+1 = rhs */
+      for (int i = 1; i < m - 1; ++i) {
+        double hl = time[i] - time[i - 1], hr = time[i + 1] - time[i];
+        sub[i] = hl;
+        dia[i] = 2.0 * (hl + hr);
+        sup[i] = hr;
+        rhs[i] = 6.0 * ((yv[i + 1] - yv[i]) / hr - (yv[i] - yv[i - 1]) / hl);
+      }
+      double g0 = 0.0, g1 = 0.0;  /* third derivatives at the two ends */
+      if (m >= 4) {
+        g0 = 6.0 * oracle_third_divided_difference(time, yv);
+        g1 = 6.0 * oracle_third_divided_difference(time + (m - 4), yv + (m - 4));
+      }
+      sub[0] = 0.0; dia[0] = -1.0; sup[0] = 1.0;
+      rhs[0] = g0 * (time[1] - time[0]);
+      sub[m - 1] = -1.0; dia[m - 1] = 1.0; sup[m - 1] = 0.0;
+      rhs[m - 1] = g1 * (time[m - 1] - time[m - 2]);
+      /* Gaussian elimination, rows in order, then back substitution */
+      for (int i = 1; i < m; ++i) {
+        double l = sub[i] / dia[i - 1];
+        dia[i] -= l * sup[i - 1];
+        rhs[i] -= l * rhs[i - 1];
+      }
+      M[m - 1] = rhs[m - 1] / dia[m - 1];
+      for (int i = m - 2; i >= 0; --i) M[i] = (rhs[i] - sup[i] * M[i + 1]) / dia[i];
+    }
+    int seg = 0;
+    for (int k = 0; k < N; ++k) {
+      double T = (k == N - 1) ? t1 : t0 + (double)k * step;
+      while (seg < m - 2 && time[seg + 1] < T) ++seg;
+      double h = time[seg + 1] - time[seg];
+      double A = time[seg + 1] - T, B = T - time[seg];
+      out[(long)k * n + v] = (M[seg] * A * A * A + M[seg + 1] * B * B * B) / (6.0 * h) +
+                             (yv[seg] - M[seg] * h * h / 6.0) * A / h +
+                             (yv[seg + 1] - M[seg + 1] * h * h / 6.0) * B / h;
+    }
+  }
+  free(yv); free(M); free(sub); free(dia); free(sup); free(rhs);
   return 0;
 }
 

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import workloads
-from test_oracle_pins import _brute, _rel
+from test_oracle_pins import _brute, _dense_fmm_spline, _grid, _rel
 
 MUTATIONS = {
     "weights_all_one": ("return omega == 0 ? 1.0 : 2.0;", "return 1.0;"),
@@ -33,8 +33,16 @@ MUTATIONS = {
                          "for (int v = 0; v < n1; ++v) r1[v] = 0.0;"),
     "interp_weight": ("double t = (x - xa) / (xb - xa);", "double t = (x - xa) / (xb - x0);"),
     "psi_unscaled": ("psi[(long)r * n2 + b] = f * zi;", "psi[(long)r * n2 + b] = norm * zi;"),
-    "perturbation_grid": ("double step = (t1 - t0) / (double)(N - 1);",
-                          "double step = (t1 - t0) / (double)N;"),
+    "perturbation_grid": ("double t0 = time[0], t1 = time[m - 1];\n  double step = (t1 - t0) / (double)(N - 1);",
+                          "double t0 = time[0], t1 = time[m - 1];\n  double step = (t1 - t0) / (double)N;"),
+    "spline_zero_end_third_derivative": ("g0 = 6.0 * oracle_third_divided_difference(time, yv);",
+                                         "g0 = 0.0;"),
+    "spline_interior_rhs_factor": ("rhs[i] = 6.0 * ((yv[i + 1] - yv[i]) / hr - (yv[i] - yv[i - 1]) / hl);",
+                                   "rhs[i] = 3.0 * ((yv[i + 1] - yv[i]) / hr - (yv[i] - yv[i - 1]) / hl);"),
+    "spline_end_interval_width": ("rhs[m - 1] = g1 * (time[m - 1] - time[m - 2]);",
+                                  "rhs[m - 1] = g1 * (time[m - 2] - time[m - 3]);"),
+    "spline_eval_weight": ("(yv[seg] - M[seg] * h * h / 6.0) * A / h",
+                           "(yv[seg] - M[seg] * h * h / 6.0) * B / h"),
 }
 
 
@@ -116,11 +124,27 @@ def _battery():
         return all(np.allclose(out[:, v], np.interp(g, t, yy[:, v].astype(np.float64)),
                                atol=1e-12) for v in range(3))
 
+    def spline_cubic():
+        t = np.array([0.0, 0.5, 1.25, 2.0, 3.5, 4.0, 5.75, 6.0])
+        c = (0.5, -1.25, 0.75, 2.0)
+        yy = np.polyval(c, t)[:, None].astype(np.float32)
+        out = oracle.interp_perturbation(t, yy, 23, method="spline")
+        return np.allclose(out[:, 0], np.polyval(c, _grid(t, 23)), rtol=0, atol=1e-10)
+
+    def spline_dense():
+        t = np.cumsum(np.random.default_rng(11).uniform(0.2, 1.5, 7))
+        yy = workloads.random_stack(7, 2, seed=12)
+        out = oracle.interp_perturbation(t, yy, 19, method="spline")
+        g = _grid(t, 19)
+        return all(np.allclose(out[:, v], _dense_fmm_spline(t, yy[:, v].astype(np.float64), g),
+                               atol=1e-9) for v in range(2))
+
     for name, fn in [("brute_homo", brute_homo), ("brute_hetero_odd", brute_hetero_odd),
                      ("brute_user_ref", brute_user_ref), ("parseval_even", parseval_even),
                      ("pearson_diag", pearson_diag), ("closed_form", closed_form),
                      ("dft_numpy", dft_numpy), ("sigma_numpy", sigma_numpy),
-                     ("interp_numpy", interp_numpy), ("interp_t_numpy", interp_t_numpy)]:
+                     ("interp_numpy", interp_numpy), ("interp_t_numpy", interp_t_numpy),
+                     ("spline_cubic", spline_cubic), ("spline_dense", spline_dense)]:
         check(name, fn)
     return failed
 

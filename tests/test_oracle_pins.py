@@ -425,6 +425,102 @@ def test_perturbation_interp_identity_and_linear_signal():
         oracle.interp_perturbation(np.array([0.0, 1.0, 1.0]), np.zeros((3, 2), np.float32), 4)
 
 
+def _grid(t, N):
+    g = t[0] + np.arange(N) * ((t[-1] - t[0]) / (N - 1))
+    g[-1] = t[-1]
+    return g
+
+
+def test_spline_reproduces_cubic_polynomials():
+    """fmm end conditions (reading R13): the third derivative at each end is that
+    of the cubic through four end points, so any cubic is reproduced exactly --
+    natural or zero-third-derivative ends would bend it.  Dyadic knots and
+    coefficients keep the FP32 inputs exact."""
+    t = np.array([0.0, 0.5, 1.25, 2.0, 3.5, 4.0, 5.75, 6.0])
+    coeffs = [(1.0, 0.0, 0.0, 0.0), (0.5, -1.25, 0.75, 2.0), (-0.25, 2.0, 0.0, -1.0),
+              (0.0, 1.5, -0.5, 0.25), (0.0, 0.0, 3.0, 1.0)]
+    y = np.stack([np.polyval(c, t) for c in coeffs], axis=1)
+    assert np.array_equal(y.astype(np.float32).astype(np.float64), y)
+    out = oracle.interp_perturbation(t, y.astype(np.float32), 29, method="spline")
+    g = _grid(t, 29)
+    for v, c in enumerate(coeffs):
+        assert np.allclose(out[:, v], np.polyval(c, g), rtol=0, atol=1e-12 * 300)
+
+
+def test_spline_with_three_and_two_points():
+    """m = 3: zero end third derivatives leave the interpolating parabola;
+    m = 2: the line (fmm's short-input cases, reading R13)."""
+    t = np.array([1.0, 1.75, 3.0])
+    y = np.array([[2.0, -1.0], [0.5, 4.0], [3.25, 0.0]], np.float32)
+    out = oracle.interp_perturbation(t, y, 11, method="spline")
+    g = _grid(t, 11)
+    for v in range(2):
+        par = np.polyfit(t, y[:, v].astype(np.float64), 2)
+        assert np.allclose(out[:, v], np.polyval(par, g), atol=1e-12)
+    t2 = np.array([0.0, 2.0])
+    y2 = np.array([[1.0], [5.0]], np.float32)
+    assert np.allclose(oracle.interp_perturbation(t2, y2, 5, method="spline")[:, 0],
+                       1.0 + 2.0 * _grid(t2, 5), atol=1e-14)
+
+
+def _dense_fmm_spline(t, y, g):
+    """The same spline written as one dense linear system in the 4 (m-1)
+    polynomial coefficients p_i(x) = a + b (x - t_i) + c (x - t_i)^2 + d (x - t_i)^3:
+    interpolation at both ends of every interval, matching first and second
+    derivatives at inner knots, and 6 d on the first / last interval equal to the
+    third derivative of numpy.polyfit's cubic through the four end points."""
+    m = len(t)
+    nu = 4 * (m - 1)
+    A = np.zeros((nu, nu))
+    b = np.zeros(nu)
+    r = 0
+    for i in range(m - 1):
+        h = t[i + 1] - t[i]
+        A[r, 4 * i] = 1.0; b[r] = y[i]; r += 1
+        A[r, 4 * i:4 * i + 4] = [1.0, h, h * h, h ** 3]; b[r] = y[i + 1]; r += 1
+    for i in range(m - 2):
+        h = t[i + 1] - t[i]
+        A[r, 4 * i:4 * i + 4] = [0.0, 1.0, 2 * h, 3 * h * h]; A[r, 4 * (i + 1) + 1] = -1.0; r += 1
+        A[r, 4 * i:4 * i + 4] = [0.0, 0.0, 2.0, 6 * h]; A[r, 4 * (i + 1) + 2] = -2.0; r += 1
+    A[r, 3] = 6.0; b[r] = 6.0 * np.polyfit(t[:4], y[:4], 3)[0]; r += 1
+    A[r, 4 * (m - 2) + 3] = 6.0; b[r] = 6.0 * np.polyfit(t[-4:], y[-4:], 3)[0]; r += 1
+    coef = np.linalg.solve(A, b)
+    s = np.clip(np.searchsorted(t, g, side="left") - 1, 0, m - 2)
+    dx = g - t[s]
+    a, bb, c, d = (coef[4 * s + k] for k in range(4))
+    return a + bb * dx + c * dx ** 2 + d * dx ** 3
+
+
+@pytest.mark.parametrize("m", [4, 6, 11])
+def test_spline_matches_dense_piecewise_cubic_solve(m):
+    rng = np.random.default_rng(m)
+    t = np.cumsum(rng.uniform(0.2, 1.5, m))
+    y = workloads.random_stack(m, 6, seed=m + 40)
+    out = oracle.interp_perturbation(t, y, 37, method="spline")
+    g = _grid(t, 37)
+    for v in range(6):
+        ref = _dense_fmm_spline(t, y[:, v].astype(np.float64), g)
+        assert np.allclose(out[:, v], ref, rtol=0, atol=1e-9 * max(1.0, np.abs(ref).max()))
+
+
+def test_spline_knots_and_fourth_order_convergence():
+    """The grid hits every knot when N = 2m - 1 on equidistant knots: values equal
+    y exactly there; on a smooth signal the error falls ~16x per halving of h."""
+    t = np.arange(9, dtype=np.float64) * 0.25
+    y = workloads.random_stack(9, 4, seed=77)
+    out = oracle.interp_perturbation(t, y, 17, method="spline")
+    assert np.allclose(out[::2], y.astype(np.float64), atol=1e-12)
+    errs = []
+    for m in (17, 33, 65):
+        tt = np.linspace(0.0, 1.0, m)
+        f = np.sin(2 * np.pi * tt) + 0.5 * np.cos(5 * tt)
+        g = _grid(tt, 1001)
+        o = oracle.interp_perturbation(tt, f[:, None].astype(np.float32), 1001, method="spline")
+        # FP32 inputs: compare with the spline-interpolation error, not below FP32 rounding
+        errs.append(np.abs(o[:, 0] - (np.sin(2 * np.pi * g) + 0.5 * np.cos(5 * g))).max())
+    assert errs[0] / errs[1] > 10.0 and errs[1] / errs[2] > 10.0
+
+
 @pytest.mark.parametrize("reduce", [1, 2, 3, 7])
 def test_reduce_map_is_decimation(reduce):
     """Sec. 4.3 `reduce`: 1-based indices divisible by reduce == numpy slicing from reduce-1."""
