@@ -165,6 +165,28 @@ corr2d_status corr2d_preprocess(corr2d_ctx* ctx, int m, int n_raw, const double*
 corr2d_status corr2d_preprocess_perturbation(corr2d_ctx* ctx, int m, int n, const double* time,
                                              const float* y, int ld, int N, float* y_out);
 
+/* Interpolating functions for corr2d_interpolate_perturbation (Sec. 4.2: the
+ * package's Int argument; approxfun and its default, splinefun). */
+typedef enum {
+  CORR2D_INTERP_LINEAR = 0, /* approxfun: piecewise linear */
+  CORR2D_INTERP_SPLINE = 1  /* splinefun with R's default method "fmm": the C^2
+                               interpolating cubic spline whose third derivative on
+                               the first / last interval is that of the cubic through
+                               the first / last four points (3 points: the parabola,
+                               2 points: the line) */
+} corr2d_interp_method;
+
+/*
+ * corr2d_preprocess_perturbation with a choice of interpolating function
+ * (same grid, arguments and errors; the linear method gives identical
+ * results).  The spline keeps an FP64 workspace of m x n second derivatives
+ * in the context (allocated on first use; ENOMEM if that fails).  An unknown
+ * method is EINVAL.
+ */
+corr2d_status corr2d_interpolate_perturbation(corr2d_ctx* ctx, int method, int m, int n,
+                                             const double* time, const float* y, int ld, int N,
+                                             float* y_out);
+
 /*
  * Synchronous and asynchronous correlation spectra of one problem.
  *   m          perturbation steps shared by both stacks, >= 2 (the

@@ -34,13 +34,15 @@ FLAG_EXACT_SYMMETRY = 2
 FLAG_HILBERT = 4
 FLAG_UPPER_TRIANGLE = 8
 _PREC_BY_NAME = {"fp32": PREC_FP32, "split": PREC_SPLIT, "bf16": PREC_BF16}
+INTERP_LINEAR, INTERP_SPLINE = 0, 1
+_INTERP_BY_NAME = {"linear": INTERP_LINEAR, "spline": INTERP_SPLINE}
 
 EXPORTED_SYMBOLS = (
     "corr2d_params_default", "corr2d_create", "corr2d_destroy", "corr2d_set_stream",
     "corr2d_last_error", "corr2d_synchronize", "corr2d_preprocess", "corr2d_compute",
     "corr2d_compute_host", "corr2d_batch", "corr2d_version", "corr2d_set_profiling",
     "corr2d_get_timings", "corr2d_compute_noalloc", "corr2d_preprocess_perturbation",
-    "corr2d_compute_rows", "corr2d_compute_reduced",
+    "corr2d_compute_rows", "corr2d_compute_reduced", "corr2d_interpolate_perturbation",
 )
 
 
@@ -86,6 +88,7 @@ def load(path: str | None = None):
             "corr2d_synchronize": (i, [vp]),
             "corr2d_preprocess": (i, [vp, i, i, vp, vp, i, vp, vp, vp]),
             "corr2d_preprocess_perturbation": (i, [vp, i, i, vp, vp, i, i, vp]),
+            "corr2d_interpolate_perturbation": (i, [vp, i, i, i, vp, vp, i, i, vp]),
             "corr2d_compute_rows": (i, [vp, i, i, vp, i, i, vp, i, ctypes.POINTER(corr2d_params),
                                         i, i, vp, vp, ctypes.c_long]),
             "corr2d_compute_reduced": (i, [vp, i, i, vp, i, i, vp, i,
@@ -152,6 +155,10 @@ def corr2d_synchronize(ctx: int) -> None:
 
 def corr2d_preprocess_perturbation(ctx, m, n, time, y, ld, N, y_out) -> None:
     _check(ctx, load().corr2d_preprocess_perturbation(ctx, m, n, time, y, ld, N, y_out))
+
+
+def corr2d_interpolate_perturbation(ctx, method, m, n, time, y, ld, N, y_out) -> None:
+    _check(ctx, load().corr2d_interpolate_perturbation(ctx, method, m, n, time, y, ld, N, y_out))
 
 
 def corr2d_preprocess(ctx, m, n_raw, x_raw, y_raw, n_out, y_out, ref=None, dyn_out=None) -> None:
@@ -325,13 +332,14 @@ class Context:
             return res + (s1, s2 if s2 is not None else s1)
         return res
 
-    def preprocess_perturbation(self, time, y, N):
-        """Resample the m x n stack y along the perturbation axis onto N equidistant steps."""
+    def preprocess_perturbation(self, time, y, N, method="linear"):
+        """Resample the m x n stack y along the perturbation axis onto N equidistant
+        steps with the linear or the (fmm) spline interpolating function."""
         import torch
         m, n = y.shape
         out = torch.empty((N, n), dtype=torch.float32, device=y.device)
-        corr2d_preprocess_perturbation(self.handle, m, n, _ptr(time), _ptr(y), y.stride(0), N,
-                                       _ptr(out))
+        corr2d_interpolate_perturbation(self.handle, _INTERP_BY_NAME[method], m, n, _ptr(time),
+                                        _ptr(y), y.stride(0), N, _ptr(out))
         return out
 
     def preprocess(self, x_raw, y_raw, n_out, ref=None):

@@ -84,6 +84,7 @@ struct corr2d_ctx {
   BatchCache batch;
   DevBuf host_in;   // corr2d_compute_host: stacks
   DevBuf host_out;  // corr2d_compute_host: two slab pairs
+  DevBuf spline;    // perturbation-axis spline: knot tables + second derivatives
   bool fault_alloc = false;
   int fault_inject = 0;  // CORR2D_FAULT=stall: the cross-spectrum producer never arrives
   bool profiling = false;
@@ -655,6 +656,7 @@ corr2d_status corr2d_destroy(corr2d_ctx* ctx) {
   release(ctx->desc);
   release(ctx->host_in);
   release(ctx->host_out);
+  release(ctx->spline);
   release(ctx->batch.desc);
   release(ctx->batch.ops);
   if (ctx->batch.exec) cudaGraphExecDestroy(ctx->batch.exec);
@@ -717,9 +719,12 @@ corr2d_status corr2d_synchronize(corr2d_ctx* ctx) {
   return CORR2D_OK;
 }
 
-corr2d_status corr2d_preprocess_perturbation(corr2d_ctx* ctx, int m, int n, const double* time,
-                                             const float* y, int ld, int N, float* y_out) {
+corr2d_status corr2d_interpolate_perturbation(corr2d_ctx* ctx, int method, int m, int n,
+                                             const double* time, const float* y, int ld, int N,
+                                             float* y_out) {
   if (!ctx) return CORR2D_EINVAL;
+  if (method != CORR2D_INTERP_LINEAR && method != CORR2D_INTERP_SPLINE)
+    return fail(ctx, CORR2D_EINVAL, "unknown interpolation method %d", method);
   if (m < 2 || n < 1 || N < 2 || ld < n)
     return fail(ctx, CORR2D_EINVAL, "perturbation interpolation needs m >= 2, n >= 1, N >= 2, ld >= n");
   if (!time || !y || !y_out) return fail(ctx, CORR2D_EINVAL, "NULL buffer");
@@ -727,9 +732,21 @@ corr2d_status corr2d_preprocess_perturbation(corr2d_ctx* ctx, int m, int n, cons
   DeviceGuard g(ctx->device);
   for (const void* q : {(const void*)time, (const void*)y, (const void*)y_out})
     if (!is_device_ptr(q, ctx->device)) return fail(ctx, CORR2D_EINVAL, "buffers must be device memory");
-  CUDA_TRY(ctx, launch_interp_t(m, n, time, y, ld, N, y_out, ctx->d_err, ctx->stream));
+  if (method == CORR2D_INTERP_LINEAR) {
+    CUDA_TRY(ctx, launch_interp_t(m, n, time, y, ld, N, y_out, ctx->d_err, ctx->stream));
+  } else {
+    corr2d_status st = ensure(ctx, ctx->spline, spline_workspace_bytes(m, n, N));
+    if (st != CORR2D_OK) return st;
+    CUDA_TRY(ctx, launch_spline_t(m, n, time, y, ld, N, y_out, ctx->spline.p, ctx->d_err,
+                                  ctx->stream));
+  }
   ctx->err.clear();
   return CORR2D_OK;
+}
+
+corr2d_status corr2d_preprocess_perturbation(corr2d_ctx* ctx, int m, int n, const double* time,
+                                             const float* y, int ld, int N, float* y_out) {
+  return corr2d_interpolate_perturbation(ctx, CORR2D_INTERP_LINEAR, m, n, time, y, ld, N, y_out);
 }
 
 corr2d_status corr2d_preprocess(corr2d_ctx* ctx, int m, int n_raw, const double* x_raw,

@@ -154,6 +154,9 @@ cudaError_t launch_interp(int m, int n_raw, const double* x, const float* y, int
                           float* out, const float* ref, float* dyn, int* err, cudaStream_t s);
 cudaError_t launch_interp_t(int m, int n, const double* t, const float* y, long ld, int N,
                             float* out, int* err, cudaStream_t s);
+size_t spline_workspace_bytes(int m, int n, int N);
+cudaError_t launch_spline_t(int m, int n, const double* t, const float* y, long ld, int N,
+                            float* out, void* ws, int* err, cudaStream_t s);
 
 // Codes of the device error word: a bounded wait ran out, or the
 // preprocessing axis check failed.

@@ -354,6 +354,54 @@ def test_preprocess_perturbation_bit_exact_and_feeds_compute(ctx):
     assert ei.value.status == pkg.EINVAL
 
 
+@pytest.mark.parametrize("m,n,N", [(2, 5, 7), (3, 300, 2), (4, 33, 64), (5, 777, 9),
+                                   (100, 777, 128), (257, 1000, 300)])
+def test_perturbation_spline_matches_oracle(ctx, m, n, N):
+    """splinefun (fmm) along the perturbation axis: the GPU rounds the same FP64
+    spline to FP32, so every output is within one FP32 ulp of the oracle."""
+    rng = np.random.default_rng(m * 7 + N)
+    time = np.sort(rng.uniform(0.0, 5.0, m))
+    time[0], time[-1] = 0.0, 5.0
+    if m > 2:
+        time = np.unique(time)
+        assert len(time) == m
+    y = workloads.sigmoid_bands(m, n, 9, seed=m + n, baseline=1.0)
+    out = ctx.preprocess_perturbation(dev(time), dev(y), N, method="spline")
+    ctx.synchronize()
+    o = oracle.interp_perturbation(time, y, N, method="spline")
+    got = out.cpu().numpy().astype(np.float64)
+    tol = np.spacing(np.abs(o).astype(np.float32)).astype(np.float64) + 1e-12 * np.abs(y).max()
+    assert np.all(np.abs(got - o) <= tol), np.abs(got - o).max()
+    if m >= 4:  # the spline is not the line
+        lin = ctx.preprocess_perturbation(dev(time), dev(y), N)
+        ctx.synchronize()
+        assert not np.array_equal(lin.cpu().numpy(), out.cpu().numpy())
+
+
+def test_perturbation_spline_feeds_compute_and_checks_arguments(ctx):
+    import paper_1808_00685_gb300 as pkg
+    rng = np.random.default_rng(21)
+    m, n, N = 60, 500, 64
+    time = np.cumsum(rng.uniform(0.05, 0.3, m))
+    y = workloads.sigmoid_bands(m, n, 12, seed=22)
+    out = ctx.preprocess_perturbation(dev(time), dev(y), N, method="spline")
+    phi, psi = ctx.compute(out, precision="split")
+    ctx.synchronize()
+    o = oracle.interp_perturbation(time, y, N, method="spline").astype(np.float32)
+    ophi, opsi, _, _ = oracle.corr2d(o)
+    check(host(phi)[:, :n], host(psi)[:, :n], ophi, opsi, 1e-5, "spline along t")
+    bad = time.copy()
+    bad[7] = bad[6]
+    ctx.preprocess_perturbation(dev(bad), dev(y), N, method="spline")
+    with pytest.raises(pkg.Corr2dError) as ei:
+        ctx.synchronize()
+    assert ei.value.status == pkg.EINVAL
+    with pytest.raises(pkg.Corr2dError) as ei:
+        pkg.corr2d_interpolate_perturbation(ctx.handle, 7, m, n, dev(time).data_ptr(),
+                                            dev(y).data_ptr(), n, N, out.data_ptr())
+    assert ei.value.status == pkg.EINVAL
+
+
 def test_row_slabs_assemble_the_full_result(ctx):
     """Multi-GPU layout on one GPU: the rows split into 128-aligned slabs (one per
     would-be GPU), each computed independently, equal one full call bit for bit."""
