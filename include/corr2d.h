@@ -57,9 +57,11 @@ typedef enum {
   CORR2D_EUNSUPPORTED = 5  /* valid request outside what this build supports */
 } corr2d_status;
 
-/* Arithmetic of the DFT and of the cross-spectrum contraction.
- * Every precision computes the reference mean and the centering subtraction
- * in FP64 and accumulates in FP32. */
+/* Arithmetic of the DFT and of the cross-spectrum contraction.  The
+ * reference mean and the centering subtraction are computed in FP64 (FP32
+ * precision) or in double-float FP32 arithmetic, an unevaluated (hi, lo) pair
+ * accurate to about 2^-44 relative (tensor-core precisions); the centred
+ * values are then rounded to FP32, and every product accumulates in FP32. */
 typedef enum {
   CORR2D_PREC_FP32 = 0,  /* CUDA-core FP32 FMA (the plain GPU baseline) */
   CORR2D_PREC_SPLIT = 1, /* tcgen05 FP16 hi/lo split: hi*hi + hi*lo + lo*hi */
@@ -198,7 +200,9 @@ corr2d_status corr2d_interpolate_perturbation(corr2d_ctx* ctx, int method, int m
  *   params     NULL for the defaults (corr2d_params_default)
  *   phi, psi   device outputs, n1 x n2 FP32, leading dimension ldo >= n2;
  *              tensor-core precisions need ldo % 4 == 0 and 16-byte aligned
- *              phi/psi (TMA stores), else EINVAL
+ *              phi/psi (TMA stores), else EINVAL.  ldo % 32 == 0 with 128-byte
+ *              aligned phi/psi is fastest: every stored row segment is then
+ *              whole 128-byte lines (no partial-sector writes)
  *   sigma1_out, sigma2_out  device, n1 / n2 FP32 standard deviations
  *              (Eq. stdev with the chosen reference), or NULL
  * A spectral variable with sigma = 0 and alpha > 0 gets scale factor 0: its

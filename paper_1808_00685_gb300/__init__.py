@@ -297,9 +297,13 @@ class Context:
 
     @staticmethod
     def alloc_out(n1, n2, device, ld=None):
-        """Phi/Psi buffers with a leading dimension that suits TMA stores."""
+        """Phi/Psi buffers whose rows start on 128-byte boundaries (ld a multiple of
+        32 floats): every stored 32-float box row is then one whole 128-byte line.
+        With rows only 16-byte aligned, half the rows of an odd-width matrix split
+        their lines into partial 32-byte sectors, which DRAM writes read-modify-write
+        (batches of ragged problems ran ~20 % slower)."""
         import torch
-        ldo = ld or (n2 + 3) // 4 * 4
+        ldo = ld or (n2 + 31) // 32 * 32
         phi = torch.empty((n1, ldo), dtype=torch.float32, device=device)
         psi = torch.empty((n1, ldo), dtype=torch.float32, device=device)
         return phi, psi, ldo
