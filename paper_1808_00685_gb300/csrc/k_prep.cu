@@ -39,6 +39,7 @@ constexpr int PREP_JG = 8 / PREP_GROUPS;               // 8-step groups per thre
 // sum of squares (3 x 2 x 128; the min slots are reused for the epilogue row
 // maxima), per-row exponent (128 ints) and double-float reference (128 pairs)
 constexpr int PREP_SCRATCH = PREP_GROUPS * PREP_ROWS * (8 + 4 + 4 + 4) + PREP_ROWS * (4 + 8);
+constexpr uint32_t PREP_STAGING = (PREP_THREADS / 32) * 4096;  // epilogue staging boxes
 
 // Error-free sum of two floats: a + b = s + e exactly (Knuth's TwoSum).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -107,11 +108,10 @@ __host__ __device__ __forceinline__ uint32_t tmem_cols_for(int ncomp) {
   return c;
 }
 
-// Write one operand chunk (g frequencies of Re and Im, already scaled) as
-// planes: SPLIT [Re_hi Im_hi Re_lo Im_lo] (16 each), BF16 [Re Im] (32 each).
+// One operand chunk (g frequencies of Re and Im, already scaled) as planes:
+// SPLIT [Re_hi Im_hi Re_lo Im_lo] (16 each), BF16 [Re Im] (32 each).
 template <int P>
-__device__ __forceinline__ void store_chunk(uint8_t* dst, const float* re, const float* im) {
-  uint4 outv[8];
+__device__ __forceinline__ void pack_chunk(const float* re, const float* im, uint4 (&outv)[8]) {
   if (P == 2) {
     split8_f32(re, outv[0], outv[4]);
     split8_f32(re + 8, outv[1], outv[5]);
@@ -123,9 +123,26 @@ __device__ __forceinline__ void store_chunk(uint8_t* dst, const float* re, const
 #pragma unroll
     for (int q = 0; q < 4; ++q) outv[4 + q] = bf16x8_f32(im + 8 * q);
   }
-  uint4* d = (uint4*)dst;
+}
+
+// Chunk c of the warp's 32 operand rows (row nu0 + lane holds pk) to global
+// memory through the warp's 4 KB staging box.  The rows lie rowlen elements
+// apart, so each thread storing its own row would touch 32 lines per store
+// instruction; restaged (XOR-swizzled, conflict-free), every instruction
+// writes four whole 128-byte lines.
+__device__ __forceinline__ void store_rows_chunk(uint8_t* stg, const uint4 (&pk)[8], uint16_t* out,
+                                                 long rowlen, int nu0, int n, int c, int lane) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) d[q] = outv[q];
+  for (int k = 0; k < 8; ++k) *(uint4*)(stg + lane * 128 + ((k ^ (lane & 7)) << 4)) = pk[k];
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int rr = i * 4 + (lane >> 3), pc = lane & 7;
+    const uint4 v = *(const uint4*)(stg + rr * 128 + ((pc ^ (rr & 7)) << 4));
+    if (nu0 + rr < n)
+      *(uint4*)((uint8_t*)(out + (size_t)(nu0 + rr) * rowlen) + c * 128 + pc * 16) = v;
+  }
+  __syncwarp();
 }
 
 template <int P>
@@ -145,11 +162,13 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
   const WaitCtl wc{err, limit_ns};
 
   // shared memory: A planes (128 rows x 128 B each), W planes (ncomp rows x
-  // 128 B each), reduction scratch, barriers
+  // 128 B each) -- after the last MMA the epilogue's staging boxes (8 warps x
+  // 4 KB) -- then reduction scratch and barriers
   uint8_t* sA = base;
   uint8_t* sW = base + P * PREP_ROWS * 128;
   const uint32_t wbytes = (uint32_t)ncomp * 128u;
-  float* red_sh = (float*)(sW + P * wbytes);               // [2][128] sums, high parts
+  const uint32_t tiles = P * PREP_ROWS * 128 + P * wbytes;
+  float* red_sh = (float*)(base + (tiles > PREP_STAGING ? tiles : PREP_STAGING));  // [2][128] sums, high
   float* red_sl = red_sh + PREP_GROUPS * PREP_ROWS;        // [2][128] sums, low parts
   float* red_mn = red_sl + PREP_GROUPS * PREP_ROWS;
   float* red_mx = red_mn + PREP_GROUPS * PREP_ROWS;
@@ -291,6 +310,13 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
 #pragma unroll
     for (int h = 0; h < PREP_JG; ++h) {
       const int jg = g + PREP_GROUPS * h;
+      const uint32_t off = sw128_off((uint32_t)r, (uint32_t)jg);
+      if (kc * 64 + jg * 8 >= m) {  // steps past m (warp-uniform): zeros
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        *(uint4*)(sA + off) = z;
+        if (P == 2) *(uint4*)(sA + PREP_ROWS * 128 + off) = z;
+        continue;
+      }
       float v[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
@@ -308,7 +334,6 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
         ss = tsum;
         v[e] = d * fy;
       }
-      const uint32_t off = sw128_off((uint32_t)r, (uint32_t)jg);
       if (P == 2) {
         uint4 hi, lo;
         split8_f32(v, hi, lo);
@@ -376,8 +401,8 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
   const float fY = ldexpf(1.0f, eY);
   const int gsz = (P == 2) ? 16 : 32;
   const int nch = kp / gsz;
-  uint8_t* rowA = (job.outA && valid_e) ? (uint8_t*)(job.outA + (size_t)nu_e * job.rowlen) : nullptr;
-  uint8_t* rowB = (job.outB && valid_e) ? (uint8_t*)(job.outB + (size_t)nu_e * job.rowlen) : nullptr;
+  uint8_t* stg = base + warp * 4096;  // the operand tiles are free after the last MMA
+  const int nu0 = item.tile * PREP_ROWS + q * 32;
   for (int c = part; c < nch; c += PREP_GROUPS) {
     float re[32], im[32];
     if (P == 2) {
@@ -393,8 +418,12 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
 #pragma unroll
       for (int i = 0; i < 32; ++i) { re[i] = a[i] * fY; im[i] = b[i] * fY; }
     }
-    if (rowA) store_chunk<P>(rowA + (size_t)c * 128, re, im);
-    if (rowB) {
+    uint4 pk[8];
+    if (job.outA) {
+      pack_chunk<P>(re, im, pk);
+      store_rows_chunk(stg, pk, job.outA, job.rowlen, nu0, n, c, lane);
+    }
+    if (job.outB) {
       // half-spectrum weight: 1 at omega = 0 (first element of chunk 0), else 2;
       // 1 everywhere for the Hilbert variant
 #pragma unroll
@@ -403,7 +432,8 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
         re[i] *= wgt;
         im[i] *= wgt;
       }
-      store_chunk<P>(rowB + (size_t)c * 128, re, im);
+      pack_chunk<P>(re, im, pk);
+      store_rows_chunk(stg, pk, job.outB, job.rowlen, nu0, n, c, lane);
     }
   }
   if (part == 0 && valid_e) {
@@ -445,8 +475,9 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
 }
 
 static size_t prep_smem_bytes(int planes, int max_kp) {
-  size_t bytes = 1024 + (size_t)planes * PREP_ROWS * 128 + (size_t)planes * 2 * max_kp * 128 +
-                 PREP_SCRATCH + 64;
+  size_t tiles = (size_t)planes * PREP_ROWS * 128 + (size_t)planes * 2 * max_kp * 128;
+  if (tiles < PREP_STAGING) tiles = PREP_STAGING;
+  size_t bytes = 1024 + tiles + PREP_SCRATCH + 64;
   // Keep (CTAs per SM) x (TMEM columns per CTA) <= 512 so allocation never waits.
   const uint32_t cols = tmem_cols_for(2 * max_kp);
   const size_t sm_smem = 233472;  // shared memory per SM
