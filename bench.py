@@ -144,17 +144,19 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def xspec_traffic_per_launch(workload_name, precision):
+def xspec_traffic_per_launch(workload_name, precision, kernel="k_xspec_tc"):
     """DRAM bytes of one cross-spectrum launch from the committed ncu summary, if that
     summary was taken on the current kernel source (same sha256), else None."""
-    src = os.path.join(ROOT, "paper_1808_00685_gb300", "csrc", "k_xspec.cu")
+    src_name = "k_xspec_pair.cu" if kernel == "k_xspec_pair" else "k_xspec.cu"
+    src = os.path.join(ROOT, "paper_1808_00685_gb300", "csrc", src_name)
     with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()
-    summ = os.path.join(ROOT, "profiles", f"xspec_{workload_name}_{precision}.md")
+    tag = "xspec_pair" if kernel == "k_xspec_pair" else "xspec"
+    summ = os.path.join(ROOT, "profiles", f"{tag}_{workload_name}_{precision}.md")
     if not os.path.exists(summ):
         return None
     text = open(summ).read()
-    m_sha = re.search(r"k_xspec\.cu sha256:\s*([0-9a-f]{64})", text)
+    m_sha = re.search(re.escape(src_name) + r" sha256:\s*([0-9a-f]{64})", text)
     m_b = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", text)
     if not m_sha or not m_b or m_sha.group(1) != sha:
         return None
@@ -307,8 +309,10 @@ def run_ours(args, world, rank, local, pg):
                 for d1, d2, ph, ps in probs:
                     ctx.compute(d1, d2, precision=args.precision, out=(ph, ps))
         else:
+            plan = ctx.batch_plan(probs, precision=args.precision)
+
             def step():
-                ctx.batch(probs, precision=args.precision)
+                plan.run()
         xbytes = 8.0 * outputs
         desc["batched"] = not (args.no_batch or args.precision == "fp32")
         y = None
@@ -318,6 +322,9 @@ def run_ours(args, world, rank, local, pg):
         step()
     ctx.synchronize()
     torch.cuda.synchronize()
+    kind, pair_clusters = ctx.kernel_info()
+    kernel = {pkg.XSPEC_TC: "k_xspec_tc", pkg.XSPEC_TC_PAIR: "k_xspec_pair",
+              pkg.XSPEC_FP32: "k_xspec_simt"}.get(kind, "none")
     barrier(pg)
 
     sampler = ClockSampler(local)
@@ -352,10 +359,10 @@ def run_ours(args, world, rank, local, pg):
     # so the whole step time stands in for the kernel time
     x_mean = statistics.mean(xspec_ms) if per_call_timing else ms
     achieved = xbytes / (x_mean / 1e3) / 1e9
-    traffic = xspec_traffic_per_launch(args.workload, args.precision)
+    traffic = xspec_traffic_per_launch(args.workload, args.precision, kernel)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "k_xspec_tc" if args.precision != "fp32" else "k_xspec_simt",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kernel,
+                "grid": (f"{pair_clusters} CTA pairs" if kernel == "k_xspec_pair" else None),
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": xbytes,
                 "kernel_ms": round(x_mean, 4), "prep_ms": round(statistics.mean(prep_ms), 4)}
     if args.precision != "fp32":

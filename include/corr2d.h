@@ -273,7 +273,10 @@ typedef struct {
  * CUDA graph per batch layout and replayed.  host_problems is a host array of
  * `count` descriptors.  shared_params (NULL = defaults) applies to every
  * problem; its ref_mode must be CORR2D_REF_MEAN and its precision a
- * tensor-core precision.
+ * tensor-core precision.  A call whose problem list and parameters equal the
+ * previous call's (same shapes and pointers) replays the recorded graph
+ * without querying the pointers again: the buffers it names must still be
+ * allocated.
  */
 corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* host_problems,
                            const corr2d_params* shared_params);
@@ -287,6 +290,16 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hos
  * Returns EINVAL when profiling is off or nothing was recorded yet. */
 corr2d_status corr2d_set_profiling(corr2d_ctx* ctx, int on);
 corr2d_status corr2d_get_timings(corr2d_ctx* ctx, float* prep_ms, float* xspec_ms);
+
+/* Which cross-spectrum kernel the last corr2d_compute / corr2d_batch call on
+ * this context launched (CORR2D_XSPEC_* below), and how many CTA pairs the
+ * device runs at once (0: the CTA-pair kernel is unavailable).  Either output
+ * may be NULL.  The tuner times the single-CTA kernel's tile shapes and
+ * orders; the environment variable CORR2D_XSPEC=pair makes it use the CTA-pair
+ * kernel instead (=any: time both kinds, =single: the default). */
+enum { CORR2D_XSPEC_NONE = 0, CORR2D_XSPEC_TC = 1, CORR2D_XSPEC_TC_PAIR = 2,
+       CORR2D_XSPEC_FP32 = 3 };
+corr2d_status corr2d_get_kernel_info(corr2d_ctx* ctx, int* last_xspec, int* pair_clusters);
 
 /*
  * Allocation-free variant of corr2d_compute.  The paper has no counterpart:

@@ -21,7 +21,7 @@ import threading
 from ._build import build, lib_path
 
 __all__ = [
-    "Corr2dError", "Context", "load", "build", "lib_path", "EXPORTED_SYMBOLS",
+    "Corr2dError", "Context", "BatchPlan", "load", "build", "lib_path", "EXPORTED_SYMBOLS",
     "PREC_FP32", "PREC_SPLIT", "PREC_BF16", "REF_MEAN", "REF_USER", "FLAG_NO_MIRROR",
 ]
 
@@ -43,7 +43,9 @@ EXPORTED_SYMBOLS = (
     "corr2d_compute_host", "corr2d_batch", "corr2d_version", "corr2d_set_profiling",
     "corr2d_get_timings", "corr2d_compute_noalloc", "corr2d_preprocess_perturbation",
     "corr2d_compute_rows", "corr2d_compute_reduced", "corr2d_interpolate_perturbation",
+    "corr2d_get_kernel_info",
 )
+XSPEC_NONE, XSPEC_TC, XSPEC_TC_PAIR, XSPEC_FP32 = range(4)
 
 
 class corr2d_params(ctypes.Structure):
@@ -107,6 +109,7 @@ def load(path: str | None = None):
             "corr2d_set_profiling": (i, [vp, i]),
             "corr2d_get_timings": (i, [vp, ctypes.POINTER(ctypes.c_float),
                                        ctypes.POINTER(ctypes.c_float)]),
+            "corr2d_get_kernel_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -236,6 +239,34 @@ def corr2d_get_timings(ctx: int):
     return a.value, b.value
 
 
+class BatchPlan:
+    """corr2d_batch arguments for one list of problems (torch tensors), built
+    once.  The tensors must stay alive while the plan is run."""
+
+    def __init__(self, ctx: "Context", problems, params: corr2d_params):
+        self.ctx = ctx
+        self.count = len(problems)
+        self.arr = (corr2d_problem * max(self.count, 1))()
+        for i, (y1, y2, phi, psi) in enumerate(problems):
+            m, n1 = y1.shape
+            n2 = n1 if y2 is None else y2.shape[1]
+            self.arr[i] = corr2d_problem(m, n1, n2, _ptr(y1), _ptr(y2), _ptr(phi), _ptr(psi),
+                                         phi.stride(0))
+        self.params = params
+        self._keep = problems
+
+    def run(self) -> None:
+        _check(self.ctx.handle, load().corr2d_batch(self.ctx.handle, self.count, self.arr,
+                                                    ctypes.byref(self.params)))
+
+
+def corr2d_get_kernel_info(ctx: int):
+    """(last cross-spectrum kernel: XSPEC_*, co-resident CTA pairs)."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(ctx, load().corr2d_get_kernel_info(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 # ------------------------------------------------------------ torch helpers
 def _ptr(t):
     return None if t is None else t.data_ptr()
@@ -294,6 +325,10 @@ class Context:
     def timings(self):
         """(prep_ms, xspec_ms) of the last call (profiling must be on)."""
         return corr2d_get_timings(self.handle)
+
+    def kernel_info(self):
+        """(last cross-spectrum kernel: XSPEC_*, co-resident CTA pairs)."""
+        return corr2d_get_kernel_info(self.handle)
 
     @staticmethod
     def alloc_out(n1, n2, device, ld=None):
@@ -358,14 +393,14 @@ class Context:
     def batch(self, problems, precision="split", alpha=0.0, norm=0.0, no_mirror=False,
               hilbert=False):
         """problems: list of (y1, y2 or None, phi, psi) torch tensors (phi/psi n1 x ldo)."""
-        ps = []
-        for y1, y2, phi, psi in problems:
-            m, n1 = y1.shape
-            n2 = n1 if y2 is None else y2.shape[1]
-            ps.append(corr2d_problem(m, n1, n2, _ptr(y1), _ptr(y2), _ptr(phi), _ptr(psi),
-                                     phi.stride(0)))
-        corr2d_batch(self.handle, ps, make_params(precision, alpha, norm, None, None, no_mirror,
-                                                  hilbert=hilbert))
+        self.batch_plan(problems, precision, alpha, norm, no_mirror, hilbert).run()
+
+    def batch_plan(self, problems, precision="split", alpha=0.0, norm=0.0, no_mirror=False,
+                   hilbert=False) -> "BatchPlan":
+        """The descriptor array of a batch, marshalled once; ``run()`` submits it
+        (repeated runs of the same list replay the library's recorded graph)."""
+        return BatchPlan(self, problems, make_params(precision, alpha, norm, None, None,
+                                                     no_mirror, hilbert=hilbert))
 
     def compute_reduced(self, y1, y2, reduce, precision="split", alpha=0.0, norm=0.0,
                         hilbert=False, ref1=None, ref2=None):

@@ -128,6 +128,15 @@ cudaError_t launch_xspec_tc(const XProblem* d_probs, const XItem* d_items, int n
                             int planes, int grid, int* err, unsigned long long limit_ns,
                             cudaStream_t s, int inject = 0, int chunk = 1);
 
+// Cross-spectrum on CTA pairs (clusters of two, tcgen05 cta_group::2): items
+// are 256 x 128 tiles (XItem.ti = index of a 256-row pair of tiles), stack-2
+// tensor maps have 64-row boxes.  `clusters` pairs run persistently.
+cudaError_t init_xspec_pair_kernels();
+int xspec_pair_max_clusters();
+cudaError_t launch_xspec_pair(const XProblem* d_probs, const XItem* d_items, int nitems,
+                              int planes, int clusters, int* err, unsigned long long limit_ns,
+                              cudaStream_t s, int inject = 0, int chunk = 1);
+
 // FP32 CUDA-core path.
 struct SimtPrepJob {
   const float* y;

@@ -318,6 +318,43 @@ def test_batch_matches_oracle_and_single_calls(ctx):
                   f"batch m={p.m} n1={p.n1} n2={p.n2} homo={p.homo}")
 
 
+def test_batch_plan_replay_reads_current_inputs_and_new_lists_are_checked(ctx):
+    """A replayed batch (same list: the recorded graph, no pointer queries) reads
+    the inputs as they are at the time of the call; a changed list is validated."""
+    import paper_1808_00685_gb300 as pkg
+    spec = workloads.c5_spec(count=6, seed=8, m_lo=8, m_hi=90, n_lo=40, n_hi=400)
+    inputs = workloads.batch_inputs(spec, nbands=4)
+    probs = []
+    for (y1, y2), p in zip(inputs, spec.problems):
+        d1 = dev(y1)
+        d2 = None if y2 is None else dev(y2)
+        phi, psi, _ = pkg.Context.alloc_out(p.n1, p.n2, d1.device)
+        probs.append((d1, d2, phi, psi))
+    plan = ctx.batch_plan(probs, precision="split")
+    for rep in range(3):
+        scale = 1.0 + rep  # new values in the same buffers before each replay
+        for (y1, y2), (d1, d2, _, _) in zip(inputs, probs):
+            d1.copy_(dev(y1 * np.float32(scale)))
+            if d2 is not None:
+                d2.copy_(dev(y2 * np.float32(scale)))
+        plan.run()
+        ctx.synchronize()
+        for (y1, y2), p, (_, _, phi, psi) in zip(inputs, spec.problems, probs):
+            ys1 = (y1 * np.float32(scale)).astype(np.float32)
+            ys2 = None if y2 is None else (y2 * np.float32(scale)).astype(np.float32)
+            ophi, opsi, _, _ = oracle.corr2d(ys1, ys2)
+            check(host(phi)[:, :p.n2], host(psi)[:, :p.n2], ophi, opsi, 1e-5,
+                  f"replay {rep} m={p.m} n1={p.n1} n2={p.n2}")
+    # the same shapes with one output in host memory: a new list, so it is checked
+    d1, d2, phi, psi = probs[0]
+    bad = [(d1, d2, phi.cpu(), psi)] + probs[1:]
+    with pytest.raises(pkg.Corr2dError) as ei:
+        ctx.batch(bad, precision="split")
+    assert ei.value.status == pkg.EINVAL
+    plan.run()  # the valid list still runs afterwards
+    ctx.synchronize()
+
+
 def test_host_buffer_entry_point(ctx):
     y1 = workloads.random_stack(33, 300, seed=13)
     y2 = workloads.random_stack(33, 260, seed=14)
