@@ -57,6 +57,17 @@ struct LaunchPlan {
   bool pair = false;  // cross-spectrum on CTA pairs
 };
 
+// A recently used corr2d_compute launch: its key, descriptor offsets and the
+// device buffer holding its descriptors.  Calls that alternate between a few
+// buffer sets (double-buffered inputs) all find their descriptors uploaded.
+struct PlanSlot {
+  LaunchPlan plan;
+  DevBuf desc;
+  std::vector<uint8_t> desc_host;  // bytes last uploaded into desc
+  unsigned long long used = 0;     // LRU clock
+};
+constexpr int kPlanSlots = 4;
+
 struct BatchCache {
   std::vector<uint8_t> key;   // serialized problem list + params
   cudaGraphExec_t exec = nullptr;     // batched DFT launch
@@ -94,7 +105,8 @@ struct corr2d_ctx {
   bool recorded = false;
   int last_xspec = CORR2D_XSPEC_NONE;  // kernel of the last compute / batch call
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // before prep, between, after xspec
-  LaunchPlan plan;  // descriptors of the last corr2d_compute call (in `desc`)
+  PlanSlot plans[kPlanSlots];  // descriptors of recent corr2d_compute calls
+  unsigned long long plan_clock = 0;
 };
 
 namespace {
@@ -334,7 +346,6 @@ Blob pack(const std::vector<PrepJob>& jobs, const std::vector<PrepItem>& pitems,
 corr2d_status upload_blob(corr2d_ctx* ctx, DevBuf& dev, std::vector<uint8_t>& last,
                           const Blob& b) {
   if (dev.p && last == b.bytes) return CORR2D_OK;
-  if (&dev == &ctx->desc) ctx->plan.key.clear();  // the cached launch no longer matches
   corr2d_status st = ensure(ctx, dev, b.bytes.size());
   if (st != CORR2D_OK) return st;
   CUDA_TRY(ctx, cudaMemcpyAsync(dev.p, b.bytes.data(), b.bytes.size(), cudaMemcpyHostToDevice,
@@ -380,7 +391,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
                          float* psi, long ldo, int out_rows, float* sig1, float* sig2,
                          const TileChoice& tc, int ti_begin, int ti_end, int out_row_tile0,
                          bool skip_prep, DevBuf& opsbuf, DevBuf& descbuf,
-                         std::vector<uint8_t>& desc_last, LaunchPlan* cache = nullptr,
+                         std::vector<uint8_t>& desc_last, bool cached = false,
                          int cstride = 1) {
   const bool homo = (y2 == nullptr);
   const bool hilbert = (p.flags & CORR2D_FLAG_HILBERT) != 0;
@@ -416,15 +427,16 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
     }
     return CORR2D_OK;
   };
-  // A call identical to the previous one (same buffers, shapes, parameters and
+  // A call identical to a recent one (same buffers, shapes, parameters and
   // tile choice) finds its descriptors already on the device: launch directly.
   std::vector<uint8_t> key;
-  if (cache) {
+  PlanSlot* slot = nullptr;
+  if (cached) {
     auto put = [&](const void* v, size_t nbytes) {
       const uint8_t* b = (const uint8_t*)v;
       key.insert(key.end(), b, b + nbytes);
     };
-    const void* ptrs[] = {y1, y2, phi, psi, sig1, sig2, p.ref1, p.ref2, opsbuf.p, descbuf.p};
+    const void* ptrs[] = {y1, y2, phi, psi, sig1, sig2, p.ref1, p.ref2, opsbuf.p};
     const int ints[] = {m, n1, ld1, n2, ld2, out_rows, p.ref_mode, p.precision, (int)p.flags,
                         tc.bn, tc.mirror, tc.group, ti_begin, ti_end, out_row_tile0,
                         skip_prep ? 1 : 0, cstride, tc.pair};
@@ -433,8 +445,18 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
     put(&ldo, sizeof ldo);
     put(&p.norm, sizeof p.norm);
     put(&p.alpha, sizeof p.alpha);
-    if (!cache->key.empty() && cache->key == key) return launch((const uint8_t*)descbuf.p, *cache);
+    for (PlanSlot& ps : ctx->plans)
+      if (ps.desc.p && ps.plan.key == key) {
+        ps.used = ++ctx->plan_clock;
+        return launch((const uint8_t*)ps.desc.p, ps.plan);
+      }
+    slot = &ctx->plans[0];  // least recently used slot takes this call
+    for (PlanSlot& ps : ctx->plans)
+      if (ps.used < slot->used) slot = &ps;
+    slot->plan.key.clear();
   }
+  DevBuf& dbuf = slot ? slot->desc : descbuf;
+  std::vector<uint8_t>& dlast = slot ? slot->desc_host : desc_last;
   uint8_t* ops = (uint8_t*)opsbuf.p;
   uint16_t* opA = (uint16_t*)ops;
   uint16_t* opB = (uint16_t*)(ops + pl.bytesA);
@@ -496,7 +518,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
     append_tiles(xitems, 0, n1, n2, tc.bn, xp.mirror != 0, ti_begin, ti_end, tc.group);
   Blob b = pack(skip_prep ? std::vector<PrepJob>{} : jobs,
                 skip_prep ? std::vector<PrepItem>{} : pitems, probs, xitems);
-  if ((st = upload_blob(ctx, descbuf, desc_last, b)) != CORR2D_OK) return st;
+  if ((st = upload_blob(ctx, dbuf, dlast, b)) != CORR2D_OK) return st;
   LaunchPlan lp;
   lp.off_jobs = b.off_jobs;
   lp.off_pitems = b.off_pitems;
@@ -508,18 +530,12 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   lp.kp = pl.kp;
   lp.skip_prep = skip_prep;
   lp.pair = pair;
-  if (cache) {
-    // the key holds descbuf.p as it was before the upload; rebuild it if the
-    // upload moved the buffer, so that the next identical call matches
-    if (!key.empty()) {
-      const size_t at = sizeof(const void*) * 9;  // descbuf.p slot in the key
-      const void* dp = descbuf.p;
-      memcpy(key.data() + at, &dp, sizeof dp);
-    }
-    *cache = lp;
-    cache->key = key;
+  if (slot) {
+    slot->plan = lp;
+    slot->plan.key = key;
+    slot->used = ++ctx->plan_clock;
   }
-  return launch((const uint8_t*)descbuf.p, lp);
+  return launch((const uint8_t*)dbuf.p, lp);
 }
 
 corr2d_status enqueue_simt(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1, int n2,
@@ -700,6 +716,7 @@ corr2d_status corr2d_destroy(corr2d_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   release(ctx->ops);
   release(ctx->desc);
+  for (PlanSlot& ps : ctx->plans) release(ps.desc);
   release(ctx->host_in);
   release(ctx->host_out);
   release(ctx->spline);
@@ -967,7 +984,7 @@ corr2d_status corr2d_compute(corr2d_ctx* ctx, int m, int n1, const float* y1, in
     if (st != CORR2D_OK) return st;
     st = enqueue_tc(ctx, m, n1, y1, ld1, n2, homo ? nullptr : y2, ld2, p, phi, psi, ldo, n1,
                     sigma1_out, homo ? nullptr : sigma2_out, tc, 0, (n1 + TILE_M - 1) / TILE_M, 0,
-                    false, ctx->ops, ctx->desc, ctx->desc_host, &ctx->plan);
+                    false, ctx->ops, ctx->desc, ctx->desc_host, true);
   }
   if (st != CORR2D_OK) return st;
   if (homo && sigma2_out && sigma1_out)
@@ -1009,7 +1026,7 @@ corr2d_status corr2d_compute_reduced(corr2d_ctx* ctx, int m, int n1, const float
   TileChoice tc{128, homo ? 1 : 0, 0};
   st = enqueue_tc(ctx, m, n1r, y1s, ld1, n2r, y2s, ld2, p, phi_r, psi_r, ldr, n1r, nullptr,
                   nullptr, tc, 0, (n1r + TILE_M - 1) / TILE_M, 0, false, ctx->ops, ctx->desc,
-                  ctx->desc_host, nullptr, reduce);
+                  ctx->desc_host, false, reduce);
   if (st != CORR2D_OK) return st;
   ctx->err.clear();
   return CORR2D_OK;

@@ -231,6 +231,29 @@ def test_repeated_calls_reuse_descriptors_correctly(ctx):
         da.copy_(torch.from_numpy(ya))
 
 
+def test_plan_cache_cycles_through_more_buffer_sets_than_slots(ctx):
+    """Recent launches keep their descriptors (a few slots, least recently used
+    replaced): cycling through six buffer sets of two shapes, hetero and homo,
+    must give every call the result of its own inputs."""
+    import paper_1808_00685_gb300 as pkg
+    sets = []
+    for i in range(6):
+        n1 = 200 if i % 2 else 260
+        y1 = workloads.random_stack(24, n1, seed=400 + i)
+        y2 = None if i % 3 == 0 else workloads.random_stack(24, 150, seed=500 + i)
+        n2 = n1 if y2 is None else 150
+        o = pkg.Context.alloc_out(n1, n2, torch.device("cuda"))
+        sets.append((y1, y2, dev(y1), None if y2 is None else dev(y2), o, n2))
+    for rnd in range(3):
+        order = list(range(6)) if rnd != 1 else [0, 1, 0, 1, 2, 0, 3, 4, 5, 1]
+        for i in order:
+            y1, y2, d1, d2, o, n2 = sets[i]
+            phi, psi = ctx.compute(d1, d2, out=o[:2])
+            ctx.synchronize()
+            ophi, opsi, _, _ = oracle.corr2d(y1, y2)
+            check(host(phi)[:, :n2], host(psi)[:, :n2], ophi, opsi, 1e-5, f"round {rnd} set {i}")
+
+
 def test_self_hetero_matches_homo(ctx):
     y = workloads.random_stack(30, 260, seed=8)
     a = run(ctx, y, precision="split", no_mirror=True)
@@ -316,6 +339,47 @@ def test_batch_matches_oracle_and_single_calls(ctx):
             ophi, opsi, _, _ = oracle.corr2d(y1, y2)
             check(host(phi)[:, :p.n2], host(psi)[:, :p.n2], ophi, opsi, 1e-5,
                   f"batch m={p.m} n1={p.n1} n2={p.n2} homo={p.homo}")
+
+
+def test_c5_full_batch_sampled_outputs(ctx):
+    """The full batch of 512 problems in the benchmark's launch configuration
+    (one corr2d_batch call: tuned tile widths and run lengths, graph replay),
+    checked on sampled outputs.  Every step before the cross product acts on
+    one spectral variable at a time (mean, centering, sigma, DFT), so the
+    oracle run on the sampled columns of the stacks gives exactly those
+    entries of Phi and Psi: 4 rows x 48 columns per problem, edges included."""
+    import paper_1808_00685_gb300 as pkg
+    spec = workloads.c5_spec()
+    ins = workloads.batch_inputs(spec)
+    probs = []
+    for (y1, y2), p in zip(ins, spec.problems):
+        d1 = dev(y1)
+        d2 = None if y2 is None else dev(y2)
+        phi, psi, _ = pkg.Context.alloc_out(p.n1, p.n2, d1.device)
+        probs.append((d1, d2, phi, psi))
+    plan = ctx.batch_plan(probs, precision="split")
+    for rep in range(2):  # the second call replays the recorded graphs
+        if rep == 1:
+            for _, _, phi, psi in probs:
+                phi.fill_(float("nan"))
+                psi.fill_(float("nan"))
+        plan.run()
+        ctx.synchronize()
+    worst = 0.0
+    for i, ((y1, y2), p, (_, _, phi, psi)) in enumerate(zip(ins, spec.problems, probs)):
+        rows = workloads.sample_rows(p.n1, 4, seed=9000 + i)
+        cols = workloads.sample_rows(p.n2, 48, seed=19000 + i)
+        rt = torch.from_numpy(rows.astype(np.int64)).cuda()
+        ct = torch.from_numpy(cols.astype(np.int64)).cuda()
+        gphi = host(phi.index_select(0, rt).index_select(1, ct))
+        gpsi = host(psi.index_select(0, rt).index_select(1, ct))
+        ys2 = (y1 if y2 is None else y2)[:, cols]
+        ophi, opsi, _, _ = oracle.corr2d(np.ascontiguousarray(y1[:, rows]),
+                                         np.ascontiguousarray(ys2))
+        ep, eq = check(gphi, gpsi, ophi, opsi, 1e-5,
+                       f"batch problem {i} m={p.m} n1={p.n1} n2={p.n2} homo={p.homo}")
+        worst = max(worst, ep, eq)
+    print(f"c5 full batch: worst relative error over 512 problems {worst:.2e}")
 
 
 def test_batch_plan_replay_reads_current_inputs_and_new_lists_are_checked(ctx):

@@ -331,6 +331,27 @@ def test_row_subset_matches_full():
     assert np.array_equal(ps, p[rows]) and np.array_equal(qs, q[rows])
 
 
+@pytest.mark.parametrize("alpha", [0.0, 0.5])
+def test_sampled_columns_give_those_entries(alpha):
+    """Reference, centering, sigma (one per spectral variable, reading R5) and
+    the DFT act on each spectral variable alone, so correlating the sampled
+    columns of the stacks gives exactly the sampled entries of the full maps.
+    A per-spectrum sigma, or a reference shared between variables, breaks it.
+    (The GPU test of the full batch of 512 problems checks sampled outputs this way.)"""
+    y1 = workloads.random_stack(23, 90, seed=61, offset=2.0)
+    y2 = workloads.random_stack(23, 70, seed=62, offset=-1.0)
+    rows = np.array([0, 7, 44, 89])
+    cols = np.array([0, 3, 31, 32, 68, 69])
+    p, q, _, _ = oracle.corr2d(y1, y2, alpha=alpha)
+    ps, qs, _, _ = oracle.corr2d(np.ascontiguousarray(y1[:, rows]),
+                                 np.ascontiguousarray(y2[:, cols]), alpha=alpha)
+    assert np.array_equal(ps, p[np.ix_(rows, cols)]) and np.array_equal(qs, q[np.ix_(rows, cols)])
+    ph, qh, _, _ = oracle.corr2d(y1, alpha=alpha)
+    ps, qs, _, _ = oracle.corr2d(np.ascontiguousarray(y1[:, rows]),
+                                 np.ascontiguousarray(y1[:, cols]), alpha=alpha)
+    assert np.array_equal(ps, ph[np.ix_(rows, cols)]) and np.array_equal(qs, qh[np.ix_(rows, cols)])
+
+
 def test_invalid_arguments_rejected():
     with pytest.raises(ValueError):
         oracle.corr2d(np.zeros((1, 4), np.float32))  # m < 2: Norm divides by m - 1
