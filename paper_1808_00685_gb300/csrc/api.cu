@@ -907,13 +907,12 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
       cands.push_back(TileChoice{128, 1, 8, 1});
       cands.push_back(TileChoice{128, 1, 12, 1});
     }
-    if (want_single) {
-      cands.push_back(TileChoice{128, 1, 0});
-      cands.push_back(TileChoice{128, 1, 8});
-      cands.push_back(TileChoice{128, 1, 12});
-    }
+    if (want_single)
+      for (int g : {0, 8, 12, 16, 24}) cands.push_back(TileChoice{128, 1, g});
   }
   if (!(can_mirror && (p.flags & (CORR2D_FLAG_EXACT_SYMMETRY | CORR2D_FLAG_UPPER_TRIANGLE)))) {
+    // full tiles: for homo problems with few frequency chunks they beat the
+    // mirrored ones (the mirrored boxes' scattered rows cost DRAM efficiency)
     if (ctx->pair_clusters > 0 && want_pair) {
       cands.push_back(TileChoice{128, 0, 0, 1});
       cands.push_back(TileChoice{128, 0, 12, 1});
@@ -929,35 +928,44 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
     ctx->tuned[key] = *out;
     return CORR2D_OK;
   }
-  cudaEvent_t e0, e1;
-  CUDA_TRY(ctx, cudaEventCreate(&e0));
-  CUDA_TRY(ctx, cudaEventCreate(&e1));
-  float best = 1e30f;
-  TileChoice bestc = cands[0];
+  // Candidates are timed on the cross-spectrum launch alone (the events the
+  // library records around it), in rounds over all candidates so that drift
+  // affects them alike; the operands come from one DFT launch before the first
+  // round, which is a warm-up.  Each candidate keeps its fastest timed run.
+  const bool was_profiling = ctx->profiling;
+  ctx->profiling = true;
   const int ti_end = (n1 + TILE_M - 1) / TILE_M;
-  for (const TileChoice& c : cands) {
-    float tsum = 1e30f;
-    for (int rep = 0; rep < 3; ++rep) {  // first run warms up, the faster of two is kept
-      cudaEventRecord(e0, ctx->stream);
-      corr2d_status st = enqueue_tc(ctx, m, n1, y1, ld1, n2e, y2, ld2, p, phi, psi, ldo, n1, nullptr,
-                                    nullptr, c, 0, ti_end, 0, false, ctx->ops, ctx->desc,
-                                    ctx->desc_host);
-      if (st != CORR2D_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
-      cudaEventRecord(e1, ctx->stream);
-      cudaEventSynchronize(e1);
+  std::vector<float> best_ms(cands.size(), 1e30f);
+  corr2d_status st = CORR2D_OK;
+  const int rounds = 3;
+  for (int r = 0; r < rounds && st == CORR2D_OK; ++r) {
+    for (size_t i = 0; i < cands.size(); ++i) {
+      const bool first = (r == 0 && i == 0);
+      st = enqueue_tc(ctx, m, n1, y1, ld1, n2e, y2, ld2, p, phi, psi, ldo, n1, nullptr, nullptr,
+                      cands[i], 0, ti_end, 0, /*skip_prep=*/!first, ctx->ops, ctx->desc,
+                      ctx->desc_host);
+      if (st != CORR2D_OK) break;
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rep >= 1) tsum = std::min(tsum, ms);
+      if (cudaEventSynchronize(ctx->ev[2]) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]) != cudaSuccess) {
+        cudaGetLastError();
+        ms = 1e30f;
+      }
+      if (r > 0) best_ms[i] = std::min(best_ms[i], ms);
     }
+  }
+  ctx->profiling = was_profiling;
+  ctx->recorded = false;
+  if (st != CORR2D_OK) return st;
+  size_t bi = 0;
+  for (size_t i = 0; i < cands.size(); ++i) {
     if (getenv("CORR2D_VERBOSE"))
       fprintf(stderr, "corr2d tuner m=%d n1=%d n2=%d: bn=%d mirror=%d group=%d pair=%d -> %.4f ms\n",
-              m, n1, n2e, c.bn, c.mirror, c.group, c.pair, tsum);
-    if (tsum < best) { best = tsum; bestc = c; }
+              m, n1, n2e, cands[i].bn, cands[i].mirror, cands[i].group, cands[i].pair, best_ms[i]);
+    if (best_ms[i] < best_ms[bi]) bi = i;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  ctx->tuned[key] = bestc;
-  *out = bestc;
+  ctx->tuned[key] = cands[bi];
+  *out = cands[bi];
   return CORR2D_OK;
 }
 
@@ -1241,8 +1249,14 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
   uint8_t* ops = (uint8_t*)bc.ops.p;
   // tuned tile width per problem: bn = 64 for problems whose 128-wide tile
   // count would leave SMs idle, chosen by timing thresholds below
-  auto build = [&](int bn_threshold, std::vector<PrepJob>& jobs, std::vector<PrepItem>& pitems,
-                   std::vector<XProblem>& probs, std::vector<XItem>& xitems) -> corr2d_status {
+  // full_kp: homo problems with at most full_kp padded frequencies use full
+  // (unmirrored) tiles, unless the flags ask for exact symmetry or the upper
+  // triangle
+  const bool may_unmirror =
+      !(p.flags & (CORR2D_FLAG_EXACT_SYMMETRY | CORR2D_FLAG_UPPER_TRIANGLE));
+  auto build = [&](int bn_threshold, int full_kp, std::vector<PrepJob>& jobs,
+                   std::vector<PrepItem>& pitems, std::vector<XProblem>& probs,
+                   std::vector<XItem>& xitems) -> corr2d_status {
     jobs.clear(); pitems.clear(); probs.clear(); xitems.clear();
     for (int i = 0; i < count; ++i) {
       const corr2d_problem& q = hp[i];
@@ -1287,7 +1301,8 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
       xp.s1 = sc1; xp.s2 = sc2;
       xp.norm = (float)default_norm(p, q.m);
       xp.n1 = q.n1; xp.n2 = n2; xp.nchunks = pl.nch;
-      xp.mirror = (homo && bn == 128 && !(p.flags & CORR2D_FLAG_NO_MIRROR)) ? 1 : 0;
+      const bool full = may_unmirror && pl.kp <= full_kp;
+      xp.mirror = (homo && bn == 128 && !full && !(p.flags & CORR2D_FLAG_NO_MIRROR)) ? 1 : 0;
       xp.bn = bn;
       xp.out_row_tile0 = 0;
       xp.upper_only = (xp.mirror && (p.flags & CORR2D_FLAG_UPPER_TRIANGLE)) ? 1 : 0;
@@ -1304,13 +1319,13 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
                    (probs[i].n1 + TILE_M - 1) / TILE_M);
     return CORR2D_OK;
   };
-  auto make_graph = [&](int bn_threshold, int chunk, cudaGraphExec_t* exec,
+  auto make_graph = [&](int bn_threshold, int chunk, int full_kp, cudaGraphExec_t* exec,
                         cudaGraphExec_t* exec_x) -> corr2d_status {
     std::vector<PrepJob> jobs;
     std::vector<PrepItem> pitems;
     std::vector<XProblem> probs;
     std::vector<XItem> xitems;
-    corr2d_status s2 = build(bn_threshold, jobs, pitems, probs, xitems);
+    corr2d_status s2 = build(bn_threshold, full_kp, jobs, pitems, probs, xitems);
     if (s2 != CORR2D_OK) return s2;
     Blob b = pack(jobs, pitems, probs, xitems);
     std::vector<uint8_t> last;
@@ -1352,40 +1367,51 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
   };
   if (bc.exec) { cudaGraphExecDestroy(bc.exec); bc.exec = nullptr; }
   if (bc.exec_x) { cudaGraphExecDestroy(bc.exec_x); bc.exec_x = nullptr; }
-  // tuner: time the batch graph for each tile-width threshold, keep the fastest
-  // tuner: tile width (bn = 64 below a problem size) x run length per CTA
+  // tuner: time the batch graph for each candidate, keep the fastest:
+  // tile width (bn = 64 below a problem size) x run length per CTA x the
+  // frequency count up to which homo problems use full tiles
   const int thresholds[] = {0, 1024, 2048};
   const int chunks[] = {1, 4};
-  int best_thr = 0, best_chunk = 1;
+  const int full_kps[] = {0, 64};
+  const int nfull = may_unmirror ? 2 : 1;
+  int best_thr = 0, best_chunk = 1, best_full = 0;
   if (!getenv("CORR2D_NO_TUNE")) {
     cudaEvent_t e0, e1;
     CUDA_TRY(ctx, cudaEventCreate(&e0));
     CUDA_TRY(ctx, cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int cand = 0; cand < 6; ++cand) {
-      const int thr = thresholds[cand % 3], chunk = chunks[cand / 3];
+    for (int cand = 0; cand < 6 * nfull; ++cand) {
+      const int thr = thresholds[cand % 3], chunk = chunks[(cand / 3) % 2];
+      const int full_kp = full_kps[cand / 6];
       cudaGraphExec_t ex = nullptr, exx = nullptr;
-      if ((st = make_graph(thr, chunk, &ex, &exx)) != CORR2D_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
-      float ms = 0.f;
-      for (int rep = 0; rep < 2; ++rep) {
+      if ((st = make_graph(thr, chunk, full_kp, &ex, &exx)) != CORR2D_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return st;
+      }
+      float ms = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {  // a warm-up, then the faster of two
         cudaEventRecord(e0, ctx->stream);
         cudaGraphLaunch(ex, ctx->stream);
         cudaGraphLaunch(exx, ctx->stream);
         cudaEventRecord(e1, ctx->stream);
         cudaEventSynchronize(e1);
-        cudaEventElapsedTime(&ms, e0, e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep > 0) ms = std::min(ms, t);
       }
       cudaGraphExecDestroy(ex);
       cudaGraphExecDestroy(exx);
       if (getenv("CORR2D_VERBOSE"))
-        fprintf(stderr, "corr2d batch tuner: bn=64 below n=%d, runs of %d -> %.4f ms\n", thr,
-                chunk, ms);
-      if (ms < best) { best = ms; best_thr = thr; best_chunk = chunk; }
+        fprintf(stderr, "corr2d batch tuner: bn=64 below n=%d, runs of %d, full tiles up to %d "
+                "frequencies -> %.4f ms\n", thr, chunk, full_kp, ms);
+      if (ms < best) { best = ms; best_thr = thr; best_chunk = chunk; best_full = full_kp; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
-  if ((st = make_graph(best_thr, best_chunk, &bc.exec, &bc.exec_x)) != CORR2D_OK) return st;
+  if ((st = make_graph(best_thr, best_chunk, best_full, &bc.exec, &bc.exec_x)) != CORR2D_OK)
+    return st;
   bc.key = key;
   ctx->last_xspec = CORR2D_XSPEC_TC;
   CUDA_TRY(ctx, replay(bc.exec, bc.exec_x));
