@@ -207,6 +207,15 @@ corr2d_status corr2d_interpolate_perturbation(corr2d_ctx* ctx, int method, int m
  *              (Eq. stdev with the chosen reference), or NULL
  * A spectral variable with sigma = 0 and alpha > 0 gets scale factor 0: its
  * row and column of Phi and Psi are 0 (instead of 0/0).
+ * The first call for a shape (m, n1, n2, homo, precision, flags) tunes the
+ * tile choice on the caller's buffers: each candidate (mirrored or full tiles,
+ * tile order) runs three times and the fastest cross-spectrum launch wins;
+ * later calls reuse it.  CORR2D_NO_TUNE=1 takes the first candidate;
+ * CORR2D_TILES=bn:mirror:group:chunk forces one choice (bn 64 or 128, mirror
+ * 0/1, group 0 for row-major or G for G x G super-blocks, chunk >= 1 list
+ * entries per CTA at a time).  Repeated calls with the same buffers and
+ * arguments (up to four recent sets) launch from descriptors already on the
+ * device.
  */
 corr2d_status corr2d_compute(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1, int n2,
                              const float* y2, int ld2, const corr2d_params* params, float* phi,

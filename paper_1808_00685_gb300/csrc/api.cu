@@ -45,6 +45,7 @@ struct TileChoice {
   int mirror = 1;
   int group = 0;  // tile order: 0 row-major, G > 0: G x G tile super-blocks
   int pair = 0;   // 1: CTA-pair kernel (256 x 128 items, bn = 128)
+  int chunk = 1;  // consecutive list entries each CTA takes at a time
 };
 
 // Device descriptors of the last corr2d_compute call and the arguments they
@@ -55,6 +56,7 @@ struct LaunchPlan {
   int npitems = 0, nxitems = 0, planes = 0, kp = 0;
   bool skip_prep = false;
   bool pair = false;  // cross-spectrum on CTA pairs
+  int chunk = 1;      // run length of list entries per CTA
 };
 
 // A recently used corr2d_compute launch: its key, descriptor offsets and the
@@ -420,7 +422,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
       CUDA_TRY(ctx, launch_xspec_tc((const XProblem*)(d + lp.off_probs),
                                     (const XItem*)(d + lp.off_xitems), lp.nxitems, lp.planes,
                                     ctx->sm_count, ctx->d_err, ctx->limit_ns, ctx->stream,
-                                    ctx->fault_inject));
+                                    ctx->fault_inject, lp.chunk));
     if (ctx->profiling) {
       cudaEventRecord(ctx->ev[2], ctx->stream);
       ctx->recorded = true;
@@ -439,7 +441,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
     const void* ptrs[] = {y1, y2, phi, psi, sig1, sig2, p.ref1, p.ref2, opsbuf.p};
     const int ints[] = {m, n1, ld1, n2, ld2, out_rows, p.ref_mode, p.precision, (int)p.flags,
                         tc.bn, tc.mirror, tc.group, ti_begin, ti_end, out_row_tile0,
-                        skip_prep ? 1 : 0, cstride, tc.pair};
+                        skip_prep ? 1 : 0, cstride, tc.pair, tc.chunk};
     put(ptrs, sizeof ptrs);
     put(ints, sizeof ints);
     put(&ldo, sizeof ldo);
@@ -530,6 +532,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   lp.kp = pl.kp;
   lp.skip_prep = skip_prep;
   lp.pair = pair;
+  lp.chunk = pair ? 1 : std::max(1, tc.chunk);
   if (slot) {
     slot->plan = lp;
     slot->plan.key = key;
@@ -897,6 +900,18 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
   auto key = std::make_tuple(m, n1, n2e, homo ? 1 : 0,
                              flag_bits + 16 * p.precision +
                                  256 * ((want_pair ? 1 : 0) + (want_single ? 2 : 0)));
+  // CORR2D_TILES=bn:mirror:group:chunk forces one tile choice (tests of every
+  // order); it is not cached
+  if (const char* ft = getenv("CORR2D_TILES")) {
+    TileChoice c;
+    if (sscanf(ft, "%d:%d:%d:%d", &c.bn, &c.mirror, &c.group, &c.chunk) == 4 &&
+        (c.bn == 64 || c.bn == 128) && c.group >= 0 && c.chunk >= 1) {
+      if (!homo || (p.flags & CORR2D_FLAG_NO_MIRROR)) c.mirror = 0;
+      *out = c;
+      return CORR2D_OK;
+    }
+    return fail(ctx, CORR2D_EINVAL, "CORR2D_TILES must be bn:mirror:group:chunk (bn 64 or 128)");
+  }
   auto it = ctx->tuned.find(key);
   if (it != ctx->tuned.end()) { *out = it->second; return CORR2D_OK; }
   std::vector<TileChoice> cands;
@@ -907,6 +922,9 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
       cands.push_back(TileChoice{128, 1, 8, 1});
       cands.push_back(TileChoice{128, 1, 12, 1});
     }
+    // (column strips, and runs of consecutive tiles per CTA, measured 7 % slower
+    // than super-blocks on homo m=256 n=32768: concurrency across CTAs, not
+    // locality in time, decides the DRAM efficiency of the mirrored stores)
     if (want_single)
       for (int g : {0, 8, 12, 16, 24}) cands.push_back(TileChoice{128, 1, g});
   }
@@ -960,8 +978,9 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
   size_t bi = 0;
   for (size_t i = 0; i < cands.size(); ++i) {
     if (getenv("CORR2D_VERBOSE"))
-      fprintf(stderr, "corr2d tuner m=%d n1=%d n2=%d: bn=%d mirror=%d group=%d pair=%d -> %.4f ms\n",
-              m, n1, n2e, cands[i].bn, cands[i].mirror, cands[i].group, cands[i].pair, best_ms[i]);
+      fprintf(stderr, "corr2d tuner m=%d n1=%d n2=%d: bn=%d mirror=%d group=%d chunk=%d pair=%d -> %.4f ms\n",
+              m, n1, n2e, cands[i].bn, cands[i].mirror, cands[i].group, cands[i].chunk,
+              cands[i].pair, best_ms[i]);
     if (best_ms[i] < best_ms[bi]) bi = i;
   }
   ctx->tuned[key] = cands[bi];

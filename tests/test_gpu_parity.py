@@ -254,6 +254,30 @@ def test_plan_cache_cycles_through_more_buffer_sets_than_slots(ctx):
             check(host(phi)[:, :n2], host(psi)[:, :n2], ophi, opsi, 1e-5, f"round {rnd} set {i}")
 
 
+@pytest.mark.parametrize("tiles", ["128:1:0:1", "128:1:8:1", "128:1:12:1", "128:1:16:1",
+                                   "128:1:24:1", "128:1:8:4", "128:0:0:1", "128:0:12:1",
+                                   "64:0:0:1"])
+def test_every_tile_order_gives_the_oracle_result(ctx, tiles):
+    """Each tile choice the tuner may pick (width, mirror, order: row-major or
+    G x G super-blocks; run length per CTA), forced through CORR2D_TILES, on
+    ragged homo and hetero problems."""
+    import os
+    y1 = workloads.random_stack(40, 700, seed=71)
+    y2 = workloads.random_stack(40, 530, seed=72)
+    os.environ["CORR2D_TILES"] = tiles
+    try:
+        phi, psi = run(ctx, y1, precision="split")
+        hphi, hpsi = run(ctx, y1, y2, precision="split")
+    finally:
+        del os.environ["CORR2D_TILES"]
+    ophi, opsi, _, _ = oracle.corr2d(y1)
+    check(phi, psi, ophi, opsi, 1e-5, f"homo tiles {tiles}")
+    if tiles.split(":")[1] == "1" and tiles.startswith("128"):  # mirrored: exact symmetry
+        assert np.array_equal(phi, phi.T) and np.array_equal(psi, -psi.T)
+    ophi, opsi, _, _ = oracle.corr2d(y1, y2)
+    check(hphi, hpsi, ophi, opsi, 1e-5, f"hetero tiles {tiles}")
+
+
 def test_self_hetero_matches_homo(ctx):
     y = workloads.random_stack(30, 260, seed=8)
     a = run(ctx, y, precision="split", no_mirror=True)
