@@ -546,7 +546,9 @@ corr2d_status enqueue_simt(corr2d_ctx* ctx, int m, int n1, const float* y1, int 
                            float* psi, long ldo, float* sig1, float* sig2) {
   const bool homo = (y2 == nullptr);
   const int kp1 = freq_count(m);
-  const size_t plane1 = align_up((size_t)kp1 * n1 * 4, 256), plane2 = align_up((size_t)kp1 * n2 * 4, 256);
+  // frequency-major planes with rows padded to 32 floats (16-byte aligned copies)
+  const int ldp1 = (n1 + 31) / 32 * 32, ldp2 = (n2 + 31) / 32 * 32;
+  const size_t plane1 = align_up((size_t)kp1 * ldp1 * 4, 256), plane2 = align_up((size_t)kp1 * ldp2 * 4, 256);
   const size_t total = 2 * plane1 + 2 * plane2 + align_up((size_t)n1 * 4, 256) + align_up((size_t)n2 * 4, 256);
   corr2d_status st = ensure(ctx, ctx->ops, total);
   if (st != CORR2D_OK) return st;
@@ -561,6 +563,7 @@ corr2d_status enqueue_simt(corr2d_ctx* ctx, int m, int n1, const float* y1, int 
   float* s2 = homo ? s1 : (float*)w;
   SimtPrepJob j{};
   j.y = y1; j.ld = ld1; j.m = m; j.n = n1; j.kp1 = kp1; j.alpha = p.alpha; j.tw = tw;
+  j.ldp = ldp1;
   j.ref = p.ref_mode == CORR2D_REF_USER ? p.ref1 : nullptr;
   j.yr = yr1; j.yi = yi1; j.scale = s1; j.sigma_out = sig1;
   j.yrw = homo ? yr2 : nullptr; j.yiw = homo ? yi2 : nullptr;
@@ -569,6 +572,7 @@ corr2d_status enqueue_simt(corr2d_ctx* ctx, int m, int n1, const float* y1, int 
   if (!homo) {
     SimtPrepJob k = j;
     k.y = y2; k.ld = ld2; k.n = n2; k.ref = p.ref_mode == CORR2D_REF_USER ? p.ref2 : nullptr;
+    k.ldp = ldp2;
     // only the weighted planes of stack 2 are read by the cross-spectrum
     k.yr = nullptr; k.yi = nullptr; k.yrw = yr2; k.yiw = yi2; k.scale = s2; k.sigma_out = sig2;
     CUDA_TRY(ctx, launch_prep_simt(k, ctx->stream));
@@ -577,7 +581,8 @@ corr2d_status enqueue_simt(corr2d_ctx* ctx, int m, int n1, const float* y1, int 
   const bool mirror = homo && !(p.flags & CORR2D_FLAG_NO_MIRROR);
   if (ctx->profiling) cudaEventRecord(ctx->ev[1], ctx->stream);
   ctx->last_xspec = CORR2D_XSPEC_FP32;
-  CUDA_TRY(ctx, launch_xspec_simt(kp1, n1, homo ? n1 : n2, yr1, yi1, yr2, yi2, s1, s2, norm, phi,
+  CUDA_TRY(ctx, launch_xspec_simt(kp1, n1, homo ? n1 : n2, ldp1, homo ? ldp1 : ldp2, yr1, yi1,
+                                  yr2, yi2, s1, s2, norm, phi,
                                   psi, ldo, mirror, ctx->stream));
   if (ctx->profiling) {
     cudaEventRecord(ctx->ev[2], ctx->stream);

@@ -150,13 +150,15 @@ struct SimtPrepJob {
   const float* tw;  // 2*m: cos(2 pi r/m), sin(2 pi r/m)
   long ld;
   int m, n, kp1;
+  int ldp;        // plane row pitch (>= n, a multiple of 32: 16-byte aligned rows)
   double alpha;
 };
 cudaError_t launch_prep_simt(const SimtPrepJob& job, cudaStream_t s);
-cudaError_t launch_xspec_simt(int kp1, int n1, int n2, const float* yr1, const float* yi1,
-                              const float* yr2w, const float* yi2w, const float* s1,
-                              const float* s2, float norm, float* phi, float* psi, long ldo,
-                              bool mirror, cudaStream_t s);
+// Planes: kp1 rows of pitch ldp1 (stack 1) / ldp2 (stack 2), multiples of 4.
+cudaError_t launch_xspec_simt(int kp1, int n1, int n2, int ldp1, int ldp2, const float* yr1,
+                              const float* yi1, const float* yr2w, const float* yi2w,
+                              const float* s1, const float* s2, float norm, float* phi,
+                              float* psi, long ldo, bool mirror, cudaStream_t s);
 
 // Preprocessing.
 cudaError_t launch_interp(int m, int n_raw, const double* x, const float* y, int n_out,

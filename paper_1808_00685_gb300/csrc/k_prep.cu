@@ -555,14 +555,15 @@ __global__ void __launch_bounds__(256) k_prep_simt(SimtPrepJob job) {
       if (rr >= m) rr -= m;
     }
     if (valid) {
+      const size_t at = (size_t)w * job.ldp + nu;
       if (job.yr) {
-        job.yr[(size_t)w * n + nu] = re;
-        job.yi[(size_t)w * n + nu] = im;
+        job.yr[at] = re;
+        job.yi[at] = im;
       }
       if (job.yrw) {
         float wt = (w == 0) ? 1.f : 2.f;
-        job.yrw[(size_t)w * n + nu] = wt * re;
-        job.yiw[(size_t)w * n + nu] = wt * im;
+        job.yrw[at] = wt * re;
+        job.yiw[at] = wt * im;
       }
     }
   }
