@@ -272,7 +272,8 @@ def run_ours(args, world, rank, local, pg):
 
         def step():
             ctx.compute(yd, precision=args.precision, out=(phi, psi))
-        xbytes = 8.0 * n * n + 2.0 * n * rowlen_elems(m, args.precision) * 2
+        # Phi and Psi stored, the homo problem's one operand row set read once
+        xbytes = 8.0 * n * n + 1.0 * n * rowlen_elems(m, args.precision) * 2
     elif args.workload == "c3":
         raw = inputs
         x1, y1r = torch.from_numpy(raw.x1).to(device), torch.from_numpy(raw.y1).to(device)

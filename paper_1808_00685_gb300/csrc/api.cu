@@ -377,11 +377,11 @@ TcPlan plan_tc(int m, int n1, int n2, bool homo, int precision, bool hilbert = f
   p.nch = p.kp / freq_group(p.planes);
   p.rowlen = p.nch * CHUNK_ELEMS;
   p.bytesA = align_up((size_t)n1 * p.rowlen * 2, 1024);
-  p.bytesB = align_up((size_t)n2 * p.rowlen * 2, 1024);
+  // homo FT problems share one row set for both operands
+  p.bytesB = (homo && !hilbert) ? 0 : align_up((size_t)n2 * p.rowlen * 2, 1024);
   p.off_s1 = p.bytesA + p.bytesB;
   p.off_s2 = p.off_s1 + align_up((size_t)n1 * 4, 256);
   p.total = p.off_s2 + align_up((size_t)n2 * 4, 256);
-  (void)homo;
   return p;
 }
 
@@ -461,7 +461,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   std::vector<uint8_t>& dlast = slot ? slot->desc_host : desc_last;
   uint8_t* ops = (uint8_t*)opsbuf.p;
   uint16_t* opA = (uint16_t*)ops;
-  uint16_t* opB = (uint16_t*)(ops + pl.bytesA);
+  uint16_t* opB = (homo && !hilbert) ? opA : (uint16_t*)(ops + pl.bytesA);
   float* s1 = (float*)(ops + pl.off_s1);
   float* s2 = homo ? s1 : (float*)(ops + pl.off_s2);
 
@@ -481,7 +481,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   const float* r1 = p.ref_mode == CORR2D_REF_USER ? p.ref1 : nullptr;
   const float* r2 = p.ref_mode == CORR2D_REF_USER ? (homo ? p.ref1 : p.ref2) : nullptr;
   if (homo && !hilbert) {
-    mkjob(y1, ld1, n1, r1, opA, opB, s1, sig1, wtab);
+    mkjob(y1, ld1, n1, r1, opA, nullptr, s1, sig1, wtab);  // opB == opA
   } else if (homo) {
     // the two operands of the Hilbert variant use different matrices
     mkjob(y1, ld1, n1, r1, opA, nullptr, s1, sig1, wtab);
@@ -1293,7 +1293,7 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
       if (s2 != CORR2D_OK) return s2;
       if (hilbert && (s2 = get_twiddles(ctx, q.m, planes, &wtab_b, XF_HT_B)) != CORR2D_OK) return s2;
       uint16_t* opA = (uint16_t*)(ops + offA[i]);
-      uint16_t* opB = (uint16_t*)(ops + offB[i]);
+      uint16_t* opB = (homo && !hilbert) ? opA : (uint16_t*)(ops + offB[i]);
       float* sc1 = (float*)(ops + offS1[i]);
       float* sc2 = homo ? sc1 : (float*)(ops + offS2[i]);
       auto mkjob = [&](const float* y, int n, uint16_t* a, uint16_t* b, float* sc,
@@ -1307,7 +1307,7 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
         for (int t = 0; t < (n + PREP_ROWS - 1) / PREP_ROWS; ++t) pitems.push_back(PrepItem{id, t});
       };
       if (homo && !hilbert) {
-        mkjob(q.y1, q.n1, opA, opB, sc1, wtab);
+        mkjob(q.y1, q.n1, opA, nullptr, sc1, wtab);  // opB == opA
       } else if (homo) {
         mkjob(q.y1, q.n1, opA, nullptr, sc1, wtab);
         mkjob(q.y1, q.n1, nullptr, opB, sc1, wtab_b);

@@ -16,9 +16,10 @@ namespace c2d {
 // covering g frequencies:
 //   SPLIT (FP16 hi/lo, g = 16): [Re_hi(16) Im_hi(16) Re_lo(16) Im_lo(16)]
 //   BF16  (g = 32):             [Re(32) Im(32)]
-// with hi = fp16(v), lo = fp16(v - hi).  The "B" operand of stack 2 carries
-// the half-spectrum weight w (1 for omega = 0, else 2); the "A" operand of
-// stack 1 does not.  A chunk is exactly one 128-byte swizzle row, so one TMA
+// with hi = fp16(v), lo = fp16(v - hi).  Both operands carry the square root
+// of the half-spectrum weight w (1 for omega = 0, else 2), so a stack-1 row
+// times a stack-2 row carries w, and a homo problem uses one row set for both
+// operands.  A chunk is exactly one 128-byte swizzle row, so one TMA
 // box of 64 elements x rows lands in shared memory ready for tcgen05.mma.
 // ----------------------------------------------------------------------------
 constexpr int CHUNK_ELEMS = 64;   // 16-bit elements per 128-byte chunk
@@ -59,8 +60,8 @@ size_t make_transform(int m, int planes, int kind, uint8_t* out);
 struct PrepJob {
   const float* y;          // m x n, leading dimension ld
   const float* ref;        // user reference (nullable -> perturbation mean)
-  uint16_t* outA;          // unweighted operand rows (nullable)
-  uint16_t* outB;          // weighted operand rows (nullable)
+  uint16_t* outA;          // operand rows of stack 1 (nullable)
+  uint16_t* outB;          // operand rows of stack 2 (nullable; may equal outA)
   float* scale;            // n: sigma^-alpha * 2^-E(nu)
   float* sigma_out;        // n (nullable)
   const uint8_t* wtab;     // pre-swizzled twiddles of this m (see make_twiddles)
@@ -69,8 +70,8 @@ struct PrepJob {
   int kp;                  // K'p
   int jchunks;             // ceil(m / 64)
   int rowlen;              // operand row length in elements
-  int plain_weights;       // 1: outB gets weight 1 everywhere (Hilbert variant);
-                           // 0: the half-spectrum weights 1 (omega = 0) / 2
+  int plain_weights;       // 1: weight 1 everywhere (Hilbert variant); 0: rows
+                           // carry sqrt of the half-spectrum weights 1 / 2
   int cstride_m1;          // column stride of y (and ref) minus 1: variable nu is
                            // column nu * (cstride_m1 + 1) (decimated preview)
   int pad2_;

@@ -418,23 +418,24 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
 #pragma unroll
       for (int i = 0; i < 32; ++i) { re[i] = a[i] * fY; im[i] = b[i] * fY; }
     }
-    uint4 pk[8];
-    if (job.outA) {
-      pack_chunk<P>(re, im, pk);
-      store_rows_chunk(stg, pk, job.outA, job.rowlen, nu0, n, c, lane);
-    }
-    if (job.outB) {
-      // half-spectrum weight: 1 at omega = 0 (first element of chunk 0), else 2;
-      // 1 everywhere for the Hilbert variant
+    // The half-spectrum weight w (1 at omega = 0, the first element of chunk
+    // 0; 2 otherwise) enters both operands as sqrt(w), so that every product
+    // of a stack-1 and a stack-2 row carries w and a homo problem needs one
+    // row set for both.  The Hilbert variant has weight 1 everywhere.
+    if (!job.plain_weights) {
+      const float rt2 = 1.41421356f;
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
-        const float wgt = (job.plain_weights || (c == 0 && i == 0)) ? 1.f : 2.f;
-        re[i] *= wgt;
-        im[i] *= wgt;
+        const float f = (c == 0 && i == 0) ? 1.f : rt2;
+        re[i] *= f;
+        im[i] *= f;
       }
-      pack_chunk<P>(re, im, pk);
-      store_rows_chunk(stg, pk, job.outB, job.rowlen, nu0, n, c, lane);
     }
+    uint4 pk[8];
+    pack_chunk<P>(re, im, pk);
+    if (job.outA) store_rows_chunk(stg, pk, job.outA, job.rowlen, nu0, n, c, lane);
+    if (job.outB && job.outB != job.outA)
+      store_rows_chunk(stg, pk, job.outB, job.rowlen, nu0, n, c, lane);
   }
   if (part == 0 && valid_e) {
     float s2sum = red_ss[lr];
