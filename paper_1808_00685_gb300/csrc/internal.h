@@ -88,7 +88,7 @@ struct PrepItem {
 // they must be 64-byte aligned.
 struct alignas(128) XProblem {
   CUtensorMap tmA;     // operand rows of stack 1: {rowlen, n1}, box {64, 128}
-  CUtensorMap tmB;     // operand rows of stack 2 (weighted): {rowlen, n2}, box {64, bn}
+  CUtensorMap tmB;     // operand rows of stack 2: {rowlen, n2}, box {64, bn}
   CUtensorMap tmPhi;   // output {n2, n1}, box {32, 32}, 128-byte swizzle
   CUtensorMap tmPsi;
   const float* s1;     // scale vectors (stack 1 / stack 2)

@@ -20,8 +20,9 @@
 //      TMEM: D(nu, c) = sum_j y~(nu, j) W(c, j); with planes hi*hi + hi*lo +
 //      lo*hi.  The twiddle chunks arrive by bulk copy.
 //   4. Epilogue (8 warps, two per TMEM lane quadrant): row maximum,
-//      power-of-two rescale, split into planes, operand rows (unweighted for
-//      stack 1, weight w = 1 / 2 for stack 2), scale sigma^-alpha 2^-E, sigma.
+//      power-of-two rescale, the square root of the half-spectrum weight
+//      (w = 1 / 2), split into planes, operand rows, scale sigma^-alpha 2^-E,
+//      sigma.
 // No FP64 arithmetic runs per element: GB300's FP64 pipe retires about one
 // operation per clock per SM, so the FP64 conversions and subtraction of a
 // plain FP64 centering bound the kernel; double-float FP32 arithmetic gives

@@ -57,20 +57,20 @@ template <int P>
 __device__ __forceinline__ void issue_chunk_mmas_pair(uint32_t d_phi, uint32_t d_psi, uint32_t a0,
                                                       uint32_t b0, uint32_t acc, uint32_t ID,
                                                       uint32_t IDN) {
-  // same operand chunk layout and products as issue_chunk_mmas (k_xspec.cu)
+  // same operand chunk layout, products and order as issue_chunk_mmas (k_xspec.cu)
   if (P == 2) {
-    mma_f16_pair(d_phi, sw128_desc(a0 + 0), sw128_desc(b0 + 0), ID, acc);     // Rh Rh
-    mma_f16_pair(d_phi, sw128_desc(a0 + 32), sw128_desc(b0 + 32), ID, 1);     // Ih Ih
-    mma_f16_pair(d_phi, sw128_desc(a0 + 0), sw128_desc(b0 + 64), ID, 1);      // Rh Rl
+    mma_f16_pair(d_phi, sw128_desc(a0 + 0), sw128_desc(b0 + 64), ID, acc);    // Rh Rl
     mma_f16_pair(d_phi, sw128_desc(a0 + 32), sw128_desc(b0 + 96), ID, 1);     // Ih Il
     mma_f16_pair(d_phi, sw128_desc(a0 + 64), sw128_desc(b0 + 0), ID, 1);      // Rl Rh
     mma_f16_pair(d_phi, sw128_desc(a0 + 96), sw128_desc(b0 + 32), ID, 1);     // Il Ih
-    mma_f16_pair(d_psi, sw128_desc(a0 + 32), sw128_desc(b0 + 0), ID, acc);    // Ih Rh
-    mma_f16_pair(d_psi, sw128_desc(a0 + 0), sw128_desc(b0 + 32), IDN, 1);     // -Rh Ih
-    mma_f16_pair(d_psi, sw128_desc(a0 + 32), sw128_desc(b0 + 64), ID, 1);     // Ih Rl
+    mma_f16_pair(d_phi, sw128_desc(a0 + 0), sw128_desc(b0 + 0), ID, 1);       // Rh Rh
+    mma_f16_pair(d_phi, sw128_desc(a0 + 32), sw128_desc(b0 + 32), ID, 1);     // Ih Ih
+    mma_f16_pair(d_psi, sw128_desc(a0 + 32), sw128_desc(b0 + 64), ID, acc);   // Ih Rl
     mma_f16_pair(d_psi, sw128_desc(a0 + 0), sw128_desc(b0 + 96), IDN, 1);     // -Rh Il
     mma_f16_pair(d_psi, sw128_desc(a0 + 96), sw128_desc(b0 + 0), ID, 1);      // Il Rh
     mma_f16_pair(d_psi, sw128_desc(a0 + 64), sw128_desc(b0 + 32), IDN, 1);    // -Rl Ih
+    mma_f16_pair(d_psi, sw128_desc(a0 + 32), sw128_desc(b0 + 0), ID, 1);      // Ih Rh
+    mma_f16_pair(d_psi, sw128_desc(a0 + 0), sw128_desc(b0 + 32), IDN, 1);     // -Rh Ih
   } else {
     mma_f16_pair(d_phi, sw128_desc(a0 + 0), sw128_desc(b0 + 0), ID, acc);
     mma_f16_pair(d_phi, sw128_desc(a0 + 32), sw128_desc(b0 + 32), ID, 1);
@@ -175,8 +175,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(XP_THREADS, 1)
           }
           const uint32_t lead_full = map_shared_rank(full_bar(stage), 0);
           const uint32_t sa = smem_u32(stages + stage * XP_STAGE_BYTES);
-          tma_load_2d_pair(sa, &pr->tmA, c * CHUNK_ELEMS, arow, lead_full, keep);
-          tma_load_2d_pair(sa + XP_A_BYTES, &pr->tmB, c * CHUNK_ELEMS, brow, lead_full, keep);
+          const int cx = (nch - 1 - c) * CHUNK_ELEMS;  // high frequencies first
+          tma_load_2d_pair(sa, &pr->tmA, cx, arow, lead_full, keep);
+          tma_load_2d_pair(sa + XP_A_BYTES, &pr->tmB, cx, brow, lead_full, keep);
           issued = true;
           if (++stage == XP_STAGES) { stage = 0; phase ^= 1u; }
         }

@@ -82,6 +82,21 @@ def test_c2_homo_offset_baseline(ctx, prec):
     assert np.all(np.diag(psi) == 0)
 
 
+@pytest.mark.parametrize("m", [384, 512])
+@pytest.mark.parametrize("kind", ["smooth", "noise"])
+def test_split_error_bar_at_the_largest_m(ctx, m, kind):
+    """The split path's error grows with the number of tensor-core additions
+    (FP32 accumulation truncates); at the largest accepted m it must still be
+    within 1e-5, for smooth (sigmoid-profile bands, baseline 10) and for
+    noise-like spectra."""
+    n = 1024
+    y = (workloads.sigmoid_bands(m, n, 40, seed=m, baseline=10.0) if kind == "smooth"
+         else workloads.random_stack(m, n, seed=m, offset=10.0))
+    phi, psi = run(ctx, y, precision="split", exact_symmetry=True)
+    ophi, opsi, _, _ = oracle.corr2d(y, nthreads=oracle.max_threads())
+    check(phi, psi, ophi, opsi, 1e-5, f"split {kind} m={m}")
+
+
 @pytest.mark.parametrize("m", [512, 257])
 def test_large_baseline_small_dynamic_part(ctx, m):
     """Baseline 1000 (stack 2: -3000) under a dynamic part of 0.01: the mean
