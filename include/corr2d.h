@@ -215,7 +215,11 @@ corr2d_status corr2d_interpolate_perturbation(corr2d_ctx* ctx, int method, int m
  * 0/1, group 0 for row-major or G for G x G super-blocks, chunk >= 1 list
  * entries per CTA at a time).  Repeated calls with the same buffers and
  * arguments (up to four recent sets) launch from descriptors already on the
- * device.
+ * device.  The launches use the context's workspace, which a later call with
+ * other shapes may reallocate: do not capture corr2d_compute into a CUDA
+ * graph that outlives such calls.  To replay one problem with the least host
+ * work, pass it to corr2d_batch as a batch of one: the batch records its own
+ * graph over buffers of its own.
  */
 corr2d_status corr2d_compute(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1, int n2,
                              const float* y2, int ld2, const corr2d_params* params, float* phi,

@@ -319,6 +319,11 @@ class Context:
     def synchronize(self):
         corr2d_synchronize(self.handle)
 
+    def set_stream(self, stream):
+        """Enqueue later calls on `stream` (a torch.cuda.Stream)."""
+        self.stream = stream
+        corr2d_set_stream(self.handle, stream.cuda_stream)
+
     def set_profiling(self, on: bool = True):
         corr2d_set_profiling(self.handle, on)
 
