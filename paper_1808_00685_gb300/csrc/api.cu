@@ -1278,7 +1278,7 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
   // triangle
   const bool may_unmirror =
       !(p.flags & (CORR2D_FLAG_EXACT_SYMMETRY | CORR2D_FLAG_UPPER_TRIANGLE));
-  auto build = [&](int bn_threshold, int full_kp, std::vector<PrepJob>& jobs,
+  auto build = [&](int bn_threshold, int full_kp, int group, std::vector<PrepJob>& jobs,
                    std::vector<PrepItem>& pitems, std::vector<XProblem>& probs,
                    std::vector<XItem>& xitems) -> corr2d_status {
     jobs.clear(); pitems.clear(); probs.clear(); xitems.clear();
@@ -1338,18 +1338,20 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
       return probs[a].nchunks > probs[b].nchunks;
     });
+    // each problem's tiles row-major, or in G x G super-blocks for mirrored
+    // problems (their transposed boxes then share DRAM pages)
     for (int i : order)
       append_tiles(xitems, i, probs[i].n1, probs[i].n2, probs[i].bn, probs[i].mirror != 0, 0,
-                   (probs[i].n1 + TILE_M - 1) / TILE_M);
+                   (probs[i].n1 + TILE_M - 1) / TILE_M, probs[i].mirror ? group : 0);
     return CORR2D_OK;
   };
-  auto make_graph = [&](int bn_threshold, int chunk, int full_kp, cudaGraphExec_t* exec,
-                        cudaGraphExec_t* exec_x) -> corr2d_status {
+  auto make_graph = [&](int bn_threshold, int chunk, int full_kp, int group,
+                        cudaGraphExec_t* exec, cudaGraphExec_t* exec_x) -> corr2d_status {
     std::vector<PrepJob> jobs;
     std::vector<PrepItem> pitems;
     std::vector<XProblem> probs;
     std::vector<XItem> xitems;
-    corr2d_status s2 = build(bn_threshold, full_kp, jobs, pitems, probs, xitems);
+    corr2d_status s2 = build(bn_threshold, full_kp, group, jobs, pitems, probs, xitems);
     if (s2 != CORR2D_OK) return s2;
     Blob b = pack(jobs, pitems, probs, xitems);
     std::vector<uint8_t> last;
@@ -1397,18 +1399,20 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
   const int thresholds[] = {0, 1024, 2048};
   const int chunks[] = {1, 4};
   const int full_kps[] = {0, 64};
+  const int groups[] = {0, 8};
   const int nfull = may_unmirror ? 2 : 1;
-  int best_thr = 0, best_chunk = 1, best_full = 0;
+  int best_thr = 0, best_chunk = 1, best_full = 0, best_group = 0;
   if (!getenv("CORR2D_NO_TUNE")) {
     cudaEvent_t e0, e1;
     CUDA_TRY(ctx, cudaEventCreate(&e0));
     CUDA_TRY(ctx, cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int cand = 0; cand < 6 * nfull; ++cand) {
+    for (int cand = 0; cand < 12 * nfull; ++cand) {
       const int thr = thresholds[cand % 3], chunk = chunks[(cand / 3) % 2];
-      const int full_kp = full_kps[cand / 6];
+      const int group = groups[(cand / 6) % 2];
+      const int full_kp = full_kps[cand / 12];
       cudaGraphExec_t ex = nullptr, exx = nullptr;
-      if ((st = make_graph(thr, chunk, full_kp, &ex, &exx)) != CORR2D_OK) {
+      if ((st = make_graph(thr, chunk, full_kp, group, &ex, &exx)) != CORR2D_OK) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         return st;
@@ -1428,13 +1432,20 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
       cudaGraphExecDestroy(exx);
       if (getenv("CORR2D_VERBOSE"))
         fprintf(stderr, "corr2d batch tuner: bn=64 below n=%d, runs of %d, full tiles up to %d "
-                "frequencies -> %.4f ms\n", thr, chunk, full_kp, ms);
-      if (ms < best) { best = ms; best_thr = thr; best_chunk = chunk; best_full = full_kp; }
+                "frequencies, mirrored order %d -> %.4f ms\n", thr, chunk, full_kp, group, ms);
+      if (ms < best) {
+        best = ms;
+        best_thr = thr;
+        best_chunk = chunk;
+        best_full = full_kp;
+        best_group = group;
+      }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
-  if ((st = make_graph(best_thr, best_chunk, best_full, &bc.exec, &bc.exec_x)) != CORR2D_OK)
+  if ((st = make_graph(best_thr, best_chunk, best_full, best_group, &bc.exec, &bc.exec_x)) !=
+      CORR2D_OK)
     return st;
   bc.key = key;
   ctx->last_xspec = CORR2D_XSPEC_TC;
