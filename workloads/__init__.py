@@ -116,6 +116,7 @@ def jittered_axis(n_raw: int, x_first: float, x_last: float, rng) -> np.ndarray:
     h = (x_last - x_first) / (n_raw - 1)
     x = x_first + h * np.arange(n_raw, dtype=np.float64)
     x[1:-1] += rng.uniform(-0.4 * h, 0.4 * h, n_raw - 2)
+    x[0], x[-1] = x_first, x_last  # exactly, not x_first + h (n_raw - 1)
     return x
 
 
@@ -197,10 +198,11 @@ def batch_inputs(spec: BatchSpec, nbands: int = 20):
 
 
 def sample_rows(n: int, count: int, seed: int) -> np.ndarray:
-    """Seeded sorted sample of distinct row indices (always includes 0 and n-1)."""
+    """Seeded sorted sample of max(count, 2) distinct row indices (all n when
+    count >= n) that always includes the first and the last row."""
+    if count >= n:
+        return np.arange(n, dtype=np.int32)
     rng = np.random.default_rng(seed)
-    count = min(count, n)
-    rows = set(rng.choice(n, size=count, replace=False).tolist())
-    rows.update({0, n - 1})
-    return np.array(sorted(rows), dtype=np.int32)[:max(count, 2)]
+    inner = rng.choice(np.arange(1, n - 1), size=max(count - 2, 0), replace=False)
+    return np.array(sorted({0, n - 1} | set(inner.tolist())), dtype=np.int32)
 
