@@ -352,18 +352,19 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
         tc_fence_after();
         const uint32_t a0 = smem_u32(sA), w0 = smem_u32(sW);
         const int ncombo = P == 2 ? 3 : 1;
+        // (A plane, W plane) products: the small hi*lo and lo*hi of all four
+        // 16-step slices first, hi*hi last, so that fewer of the accumulator's
+        // (truncating) additions happen at its full size
 #pragma unroll 1
-        for (int ks = 0; ks < 4; ++ks) {
-#pragma unroll 1
-          for (int cb = 0; cb < ncombo; ++cb) {
-            // (A plane, W plane): hi*hi, hi*lo, lo*hi
-            const int pa = (cb == 2) ? 1 : 0, pw = (cb == 1) ? 1 : 0;
-            const uint64_t ad = sw128_desc(a0 + pa * PREP_ROWS * 128 + ks * 32);
-            const uint32_t acc = (kc > 0 || ks > 0 || cb > 0) ? 1u : 0u;
-            for (int hh = 0; hh < nhalf; ++hh) {
-              const uint64_t bd = sw128_desc(w0 + pw * wbytes + hh * 256 * 128 + ks * 32);
-              mma_f16(tmem + hh * 256, ad, bd, hh ? id1 : id0, acc);
-            }
+        for (int o = 0; o < 4 * ncombo; ++o) {
+          const int cb = (ncombo == 3) ? (o < 8 ? 1 + (o & 1) : 0) : 0;
+          const int ks = (ncombo == 3) ? (o < 8 ? o >> 1 : o - 8) : o;
+          const int pa = (cb == 2) ? 1 : 0, pw = (cb == 1) ? 1 : 0;
+          const uint64_t ad = sw128_desc(a0 + pa * PREP_ROWS * 128 + ks * 32);
+          const uint32_t acc = (kc > 0 || o > 0) ? 1u : 0u;
+          for (int hh = 0; hh < nhalf; ++hh) {
+            const uint64_t bd = sw128_desc(w0 + pw * wbytes + hh * 256 * 128 + ks * 32);
+            mma_f16(tmem + hh * 256, ad, bd, hh ? id1 : id0, acc);
           }
         }
         mma_commit(mbar);
