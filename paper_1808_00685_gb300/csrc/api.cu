@@ -1,7 +1,8 @@
 // C ABI of the library (declared in include/corr2d.h): argument validation,
 // device workspace, twiddle tables, TMA descriptors, tile lists, the tile
-// tuner, batch graphs and the host-buffer path.  All arithmetic of the method
-// runs in the kernels of k_prep.cu, k_xspec.cu, k_simt.cu and k_interp.cu.
+// tuners, recent-launch descriptor cache, batch graphs and the host-buffer
+// path.  All arithmetic of the method runs in the kernels of k_prep.cu,
+// k_xspec.cu (k_xspec_pair.cu), k_simt.cu and k_interp.cu.
 #include <algorithm>
 #include <chrono>
 #include <cmath>

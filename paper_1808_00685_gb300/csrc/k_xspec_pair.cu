@@ -10,9 +10,12 @@
 // MMA instruction issued by the even CTA multiplies the 256 rows by all 128
 // columns, each CTA receiving its 128 x 128 accumulators in its own TMEM.
 // Against one CTA per 128 x 128 tile this halves the stack-2 operand bytes a
-// CTA loads and reads from shared memory per output, the resource that bounds
-// the single-CTA kernel in split precision (four shared-memory bytes per
-// output byte become three for the operands).
+// CTA loads and reads from shared memory per output (four shared-memory bytes
+// per output byte become three for the operands).  Measured on GB300 the
+// coupling of the two SMs (an MMA waits for both operand halves, a TMEM buffer
+// for both epilogues) costs more than the saved traffic: the kernel runs 2-20 %
+// slower than k_xspec_tc, so the library uses it only on request
+// (CORR2D_XSPEC=pair or =any).
 //
 // Roles (320 threads per CTA, as in k_xspec_tc):
 //   warp 0      TMA producer of this CTA's operand halves; both CTAs' loads
@@ -32,6 +35,8 @@
 
 namespace c2d {
 
+// operand stages and staging slots per epilogue warp (build-time overrides
+// for sweeps; 4 stages measured 13 % slower, 6 stages or 3 slots no faster)
 #ifndef C2D_XP_STAGES
 #define C2D_XP_STAGES 5
 #endif
