@@ -304,10 +304,11 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hos
 corr2d_status corr2d_set_profiling(corr2d_ctx* ctx, int on);
 corr2d_status corr2d_get_timings(corr2d_ctx* ctx, float* prep_ms, float* xspec_ms);
 
-/* Which cross-spectrum kernel the last corr2d_compute / corr2d_batch call on
- * this context launched (CORR2D_XSPEC_* below), and how many CTA pairs the
- * device runs at once (0: the CTA-pair kernel is unavailable).  Either output
- * may be NULL.  The tuner times the single-CTA kernel's tile shapes and
+/* Library introspection (the paper has no counterpart): which cross-spectrum
+ * kernel the last corr2d_compute / corr2d_batch call on this context launched
+ * (CORR2D_XSPEC_* below), and how many CTA pairs the device runs at once (0:
+ * the CTA-pair kernel is unavailable).  Either output may be NULL (host
+ * ints otherwise); EINVAL for a NULL context.  The tuner times the single-CTA kernel's tile shapes and
  * orders; the environment variable CORR2D_XSPEC=pair makes it use the CTA-pair
  * kernel instead (=any: time both kinds, =single: the default). */
 enum { CORR2D_XSPEC_NONE = 0, CORR2D_XSPEC_TC = 1, CORR2D_XSPEC_TC_PAIR = 2,
