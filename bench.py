@@ -147,11 +147,12 @@ def measured_peaks():
 def xspec_traffic_per_launch(workload_name, precision, kernel="k_xspec_tc"):
     """DRAM bytes of one cross-spectrum launch from the committed ncu summary, if that
     summary was taken on the current kernel source (same sha256), else None."""
-    src_name = "k_xspec_pair.cu" if kernel == "k_xspec_pair" else "k_xspec.cu"
+    src_name = {"k_xspec_pair": "k_xspec_pair.cu", "k_xspec_ta": "k_xspec_ta.cu"}.get(kernel,
+                                                                                   "k_xspec.cu")
     src = os.path.join(ROOT, "paper_1808_00685_gb300", "csrc", src_name)
     with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()
-    tag = "xspec_pair" if kernel == "k_xspec_pair" else "xspec"
+    tag = {"k_xspec_pair": "xspec_pair", "k_xspec_ta": "xspec_ta"}.get(kernel, "xspec")
     summ = os.path.join(ROOT, "profiles", f"{tag}_{workload_name}_{precision}.md")
     if not os.path.exists(summ):
         return None
@@ -325,6 +326,7 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.synchronize()
     kind, pair_clusters = ctx.kernel_info()
     kernel = {pkg.XSPEC_TC: "k_xspec_tc", pkg.XSPEC_TC_PAIR: "k_xspec_pair",
+              pkg.XSPEC_TC_TA: "k_xspec_ta",
               pkg.XSPEC_FP32: "k_xspec_simt"}.get(kind, "none")
     barrier(pg)
 

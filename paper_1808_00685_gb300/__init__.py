@@ -45,7 +45,7 @@ EXPORTED_SYMBOLS = (
     "corr2d_compute_rows", "corr2d_compute_reduced", "corr2d_interpolate_perturbation",
     "corr2d_get_kernel_info",
 )
-XSPEC_NONE, XSPEC_TC, XSPEC_TC_PAIR, XSPEC_FP32 = range(4)
+XSPEC_NONE, XSPEC_TC, XSPEC_TC_PAIR, XSPEC_FP32, XSPEC_TC_TA = range(5)
 
 
 class corr2d_params(ctypes.Structure):

@@ -47,6 +47,7 @@ struct TileChoice {
   int group = 0;  // tile order: 0 row-major, G > 0: G x G tile super-blocks
   int pair = 0;   // 1: CTA-pair kernel (256 x 128 items, bn = 128)
   int chunk = 1;  // consecutive list entries each CTA takes at a time
+  int ta = 0;     // > 0: TMEM-operand kernel (128 x 64 tiles), row segments of ta tiles
 };
 
 // Device descriptors of the last corr2d_compute call and the arguments they
@@ -57,6 +58,7 @@ struct LaunchPlan {
   int npitems = 0, nxitems = 0, planes = 0, kp = 0;
   bool skip_prep = false;
   bool pair = false;  // cross-spectrum on CTA pairs
+  bool ta = false;    // cross-spectrum with the stack-1 operand in TMEM (XSeg list)
   int chunk = 1;      // run length of list entries per CTA
 };
 
@@ -311,6 +313,15 @@ void append_pair_tiles(std::vector<XItem>& items, int prob, int n1, int n2, bool
           items.push_back(XItem{prob, (uint16_t)a, (uint16_t)tj});
 }
 
+// Row segments of the TMEM-operand kernel: each 128-row tile row split into
+// runs of at most seg column tiles of 128 (mirrored problems: tj >= ti).
+void append_segments(std::vector<XSeg>& segs, int prob, int n1, int n2, bool mirror, int seg) {
+  const int nt1 = (n1 + TILE_M - 1) / TILE_M, nt2 = (n2 + TILE_N - 1) / TILE_N;
+  for (int ti = 0; ti < nt1; ++ti)
+    for (int tj = mirror ? ti : 0; tj < nt2; tj += seg)
+      segs.push_back(XSeg{prob, (uint16_t)ti, (uint16_t)tj, (uint16_t)std::min(seg, nt2 - tj), 0});
+}
+
 // Host descriptor blob: [PrepJob...][PrepItem...][XProblem...][XItem...], each 128-aligned.
 struct Blob {
   std::vector<uint8_t> bytes;
@@ -318,8 +329,9 @@ struct Blob {
   int njobs = 0, npitems = 0, nprobs = 0, nxitems = 0;
 };
 
+template <class Item>
 Blob pack(const std::vector<PrepJob>& jobs, const std::vector<PrepItem>& pitems,
-          const std::vector<XProblem>& probs, const std::vector<XItem>& xitems) {
+          const std::vector<XProblem>& probs, const std::vector<Item>& xitems) {
   Blob b;
   size_t off = 0;
   b.off_jobs = off;
@@ -329,7 +341,7 @@ Blob pack(const std::vector<PrepJob>& jobs, const std::vector<PrepItem>& pitems,
   b.off_probs = off;
   off = align_up(off + probs.size() * sizeof(XProblem), 128);
   b.off_xitems = off;
-  off = align_up(off + xitems.size() * sizeof(XItem), 128);
+  off = align_up(off + xitems.size() * sizeof(Item), 128);
   b.bytes.assign(off, 0);
   if (!jobs.empty()) memcpy(b.bytes.data() + b.off_jobs, jobs.data(), jobs.size() * sizeof(PrepJob));
   if (!pitems.empty())
@@ -337,7 +349,7 @@ Blob pack(const std::vector<PrepJob>& jobs, const std::vector<PrepItem>& pitems,
   if (!probs.empty())
     memcpy(b.bytes.data() + b.off_probs, probs.data(), probs.size() * sizeof(XProblem));
   if (!xitems.empty())
-    memcpy(b.bytes.data() + b.off_xitems, xitems.data(), xitems.size() * sizeof(XItem));
+    memcpy(b.bytes.data() + b.off_xitems, xitems.data(), xitems.size() * sizeof(Item));
   b.njobs = (int)jobs.size();
   b.npitems = (int)pitems.size();
   b.nprobs = (int)probs.size();
@@ -413,8 +425,13 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
                                    (const PrepItem*)(d + lp.off_pitems), lp.npitems, lp.planes,
                                    lp.kp, ctx->d_err, ctx->limit_ns, ctx->stream));
     if (ctx->profiling) cudaEventRecord(ctx->ev[1], ctx->stream);
-    ctx->last_xspec = lp.pair ? CORR2D_XSPEC_TC_PAIR : CORR2D_XSPEC_TC;
-    if (lp.pair)
+    ctx->last_xspec = lp.pair ? CORR2D_XSPEC_TC_PAIR : lp.ta ? CORR2D_XSPEC_TC_TA : CORR2D_XSPEC_TC;
+    if (lp.ta)
+      CUDA_TRY(ctx, launch_xspec_ta((const XProblem*)(d + lp.off_probs),
+                                    (const XSeg*)(d + lp.off_xitems), lp.nxitems, lp.planes,
+                                    ctx->sm_count, ctx->d_err, ctx->limit_ns, ctx->stream,
+                                    ctx->fault_inject));
+    else if (lp.pair)
       CUDA_TRY(ctx, launch_xspec_pair((const XProblem*)(d + lp.off_probs),
                                       (const XItem*)(d + lp.off_xitems), lp.nxitems, lp.planes,
                                       ctx->pair_clusters, ctx->d_err, ctx->limit_ns, ctx->stream,
@@ -442,7 +459,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
     const void* ptrs[] = {y1, y2, phi, psi, sig1, sig2, p.ref1, p.ref2, opsbuf.p};
     const int ints[] = {m, n1, ld1, n2, ld2, out_rows, p.ref_mode, p.precision, (int)p.flags,
                         tc.bn, tc.mirror, tc.group, ti_begin, ti_end, out_row_tile0,
-                        skip_prep ? 1 : 0, cstride, tc.pair, tc.chunk};
+                        skip_prep ? 1 : 0, cstride, tc.pair, tc.chunk, tc.ta};
     put(ptrs, sizeof ptrs);
     put(ints, sizeof ints);
     put(&ldo, sizeof ldo);
@@ -495,11 +512,16 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   const bool pair = tc.pair && tc.bn == TILE_N && ti_begin == 0 &&
                     ti_end == (n1 + TILE_M - 1) / TILE_M && out_row_tile0 == 0 &&
                     ctx->pair_clusters > 0;
+  // the TMEM-operand kernel holds a row's stack-1 chunks in TMEM (at most
+  // TA_MAX_CHUNKS) and also computes whole problems
+  const bool ta = tc.ta > 0 && !pair && pl.nch <= TA_MAX_CHUNKS && ti_begin == 0 &&
+                  ti_end == (n1 + TILE_M - 1) / TILE_M && out_row_tile0 == 0;
+  const int bn = ta ? TILE_N : tc.bn;
   XProblem xp;
   memset(&xp, 0, sizeof xp);
   if ((st = encode_operand(ctx, &xp.tmA, opA, pl.rowlen, n1, TILE_M, pl.planes)) != CORR2D_OK) return st;
-  if ((st = encode_operand(ctx, &xp.tmB, opB, pl.rowlen, n2, pair ? tc.bn / 2 : tc.bn,
-                           pl.planes)) != CORR2D_OK)
+  if ((st = encode_operand(ctx, &xp.tmB, opB, pl.rowlen, n2, pair ? bn / 2 : bn, pl.planes)) !=
+      CORR2D_OK)
     return st;
   if ((st = encode_output(ctx, &xp.tmPhi, phi, out_rows, n2, ldo)) != CORR2D_OK) return st;
   if ((st = encode_output(ctx, &xp.tmPsi, psi, out_rows, n2, ldo)) != CORR2D_OK) return st;
@@ -509,18 +531,23 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   xp.n1 = n1;
   xp.n2 = n2;
   xp.nchunks = pl.nch;
-  xp.mirror = (homo && tc.mirror && tc.bn == TILE_M) ? 1 : 0;
-  xp.bn = tc.bn;
+  xp.mirror = (homo && tc.mirror && bn == TILE_M) ? 1 : 0;
+  xp.bn = bn;
   xp.out_row_tile0 = out_row_tile0;
   xp.upper_only = (xp.mirror && (p.flags & CORR2D_FLAG_UPPER_TRIANGLE)) ? 1 : 0;
   std::vector<XProblem> probs{xp};
   std::vector<XItem> xitems;
-  if (pair)
+  std::vector<XSeg> segs;
+  if (ta)
+    append_segments(segs, 0, n1, n2, xp.mirror != 0, tc.ta);
+  else if (pair)
     append_pair_tiles(xitems, 0, n1, n2, xp.mirror != 0, tc.group);
   else
     append_tiles(xitems, 0, n1, n2, tc.bn, xp.mirror != 0, ti_begin, ti_end, tc.group);
-  Blob b = pack(skip_prep ? std::vector<PrepJob>{} : jobs,
-                skip_prep ? std::vector<PrepItem>{} : pitems, probs, xitems);
+  Blob b = ta ? pack(skip_prep ? std::vector<PrepJob>{} : jobs,
+                     skip_prep ? std::vector<PrepItem>{} : pitems, probs, segs)
+              : pack(skip_prep ? std::vector<PrepJob>{} : jobs,
+                     skip_prep ? std::vector<PrepItem>{} : pitems, probs, xitems);
   if ((st = upload_blob(ctx, dbuf, dlast, b)) != CORR2D_OK) return st;
   LaunchPlan lp;
   lp.off_jobs = b.off_jobs;
@@ -533,7 +560,8 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   lp.kp = pl.kp;
   lp.skip_prep = skip_prep;
   lp.pair = pair;
-  lp.chunk = pair ? 1 : std::max(1, tc.chunk);
+  lp.ta = ta;
+  lp.chunk = (pair || ta) ? 1 : std::max(1, tc.chunk);
   if (slot) {
     slot->plan = lp;
     slot->plan.key = key;
@@ -696,7 +724,7 @@ corr2d_status corr2d_create(corr2d_ctx** out, int device, void* cuda_stream) {
     return fail(nullptr, CORR2D_ECUDA, "cuTensorMapEncodeTiled unavailable");
   ctx->encode = (PFN_encodeTiled)fn;
   if (init_prep_kernels() != cudaSuccess || init_xspec_kernels() != cudaSuccess ||
-      init_xspec_pair_kernels() != cudaSuccess)
+      init_xspec_pair_kernels() != cudaSuccess || init_xspec_ta_kernels() != cudaSuccess)
     return fail(nullptr, CORR2D_ECUDA, "kernel attribute setup failed: %s",
                 cudaGetErrorString(cudaGetLastError()));
   ctx->pair_clusters = getenv("CORR2D_NO_PAIR") ? 0 : xspec_pair_max_clusters();
@@ -900,23 +928,30 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
   // tuner time both (the pair kernel measured slower on every workload tried).
   const char* xk = getenv("CORR2D_XSPEC");
   const bool want_pair = xk && (strcmp(xk, "pair") == 0 || strcmp(xk, "any") == 0);
-  const bool want_single = !want_pair || strcmp(xk, "any") == 0 || ctx->pair_clusters == 0;
+  const bool want_ta = xk && (strcmp(xk, "ta") == 0 || strcmp(xk, "any") == 0) &&
+                       chunks_for(m, p.precision == CORR2D_PREC_SPLIT ? 2 : 1) <= TA_MAX_CHUNKS &&
+                       !(p.flags & CORR2D_FLAG_HILBERT);
+  const bool want_single = (!want_pair && !want_ta) || strcmp(xk, "any") == 0 ||
+                           (want_pair && ctx->pair_clusters == 0);
   const int flag_bits = (int)(p.flags & (CORR2D_FLAG_NO_MIRROR | CORR2D_FLAG_EXACT_SYMMETRY |
                                          CORR2D_FLAG_HILBERT | CORR2D_FLAG_UPPER_TRIANGLE));
   auto key = std::make_tuple(m, n1, n2e, homo ? 1 : 0,
                              flag_bits + 16 * p.precision +
-                                 256 * ((want_pair ? 1 : 0) + (want_single ? 2 : 0)));
-  // CORR2D_TILES=bn:mirror:group:chunk forces one tile choice (tests of every
-  // order); it is not cached
+                                 256 * ((want_pair ? 1 : 0) + (want_single ? 2 : 0) +
+                                        (want_ta ? 4 : 0)));
+  // CORR2D_TILES=bn:mirror:group:chunk[:seg] forces one tile choice (tests of
+  // every order; seg > 0 selects the TMEM-operand kernel); it is not cached
   if (const char* ft = getenv("CORR2D_TILES")) {
     TileChoice c;
-    if (sscanf(ft, "%d:%d:%d:%d", &c.bn, &c.mirror, &c.group, &c.chunk) == 4 &&
-        (c.bn == 64 || c.bn == 128) && c.group >= 0 && c.chunk >= 1) {
+    const int nf = sscanf(ft, "%d:%d:%d:%d:%d", &c.bn, &c.mirror, &c.group, &c.chunk, &c.ta);
+    if ((nf == 4 || nf == 5) && (c.bn == 64 || c.bn == 128) && c.group >= 0 && c.chunk >= 1 &&
+        c.ta >= 0 && c.ta <= 4096) {
       if (!homo || (p.flags & CORR2D_FLAG_NO_MIRROR)) c.mirror = 0;
       *out = c;
       return CORR2D_OK;
     }
-    return fail(ctx, CORR2D_EINVAL, "CORR2D_TILES must be bn:mirror:group:chunk (bn 64 or 128)");
+    return fail(ctx, CORR2D_EINVAL,
+                "CORR2D_TILES must be bn:mirror:group:chunk[:seg] (bn 64 or 128, seg 0..4096)");
   }
   auto it = ctx->tuned.find(key);
   if (it != ctx->tuned.end()) { *out = it->second; return CORR2D_OK; }
@@ -933,6 +968,8 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
     // locality in time, decides the DRAM efficiency of the mirrored stores)
     if (want_single)
       for (int g : {0, 8, 12, 16, 24}) cands.push_back(TileChoice{128, 1, g});
+    if (want_ta)
+      for (int sg : {8, 16, 32}) cands.push_back(TileChoice{128, 1, 0, 0, 1, sg});
   }
   if (!(can_mirror && (p.flags & (CORR2D_FLAG_EXACT_SYMMETRY | CORR2D_FLAG_UPPER_TRIANGLE)))) {
     // full tiles: for homo problems with few frequency chunks they beat the
@@ -946,6 +983,8 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
       cands.push_back(TileChoice{128, 0, 12});
       cands.push_back(TileChoice{64, 0, 0});
     }
+    if (want_ta)
+      for (int sg : {8, 16, 32}) cands.push_back(TileChoice{128, 0, 0, 0, 1, sg});
   }
   if (getenv("CORR2D_NO_TUNE") || cands.size() == 1) {
     *out = cands[0];
@@ -984,9 +1023,9 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
   size_t bi = 0;
   for (size_t i = 0; i < cands.size(); ++i) {
     if (getenv("CORR2D_VERBOSE"))
-      fprintf(stderr, "corr2d tuner m=%d n1=%d n2=%d: bn=%d mirror=%d group=%d chunk=%d pair=%d -> %.4f ms\n",
+      fprintf(stderr, "corr2d tuner m=%d n1=%d n2=%d: bn=%d mirror=%d group=%d chunk=%d pair=%d seg=%d -> %.4f ms\n",
               m, n1, n2e, cands[i].bn, cands[i].mirror, cands[i].group, cands[i].chunk,
-              cands[i].pair, best_ms[i]);
+              cands[i].pair, cands[i].ta, best_ms[i]);
     if (best_ms[i] < best_ms[bi]) bi = i;
   }
   ctx->tuned[key] = cands[bi];

@@ -129,6 +129,21 @@ cudaError_t launch_xspec_tc(const XProblem* d_probs, const XItem* d_items, int n
                             int planes, int grid, int* err, unsigned long long limit_ns,
                             cudaStream_t s, int inject = 0, int chunk = 1);
 
+// Row segment of the TMEM-operand cross-spectrum kernel: tiles (ti, tj0 ..
+// tj0 + ntj - 1) of 128 x 64 outputs that share their stack-1 rows.
+struct XSeg {
+  int prob;
+  uint16_t ti, tj0, ntj, pad_;
+};
+// Cross-spectrum with the stack-1 operand in TMEM (k_xspec_ta): segments
+// instead of tiles, stack-2 tensor maps with 64-row boxes, problems with at
+// most 8 operand chunks (m <= 256 in split precision).
+cudaError_t init_xspec_ta_kernels();
+cudaError_t launch_xspec_ta(const XProblem* d_probs, const XSeg* d_segs, int nsegs, int planes,
+                            int grid, int* err, unsigned long long limit_ns, cudaStream_t s,
+                            int inject = 0);
+constexpr int TA_MAX_CHUNKS = 8;
+
 // Cross-spectrum on CTA pairs (clusters of two, tcgen05 cta_group::2): items
 // are 256 x 128 tiles (XItem.ti = index of a 256-row pair of tiles), stack-2
 // tensor maps have 64-row boxes.  `clusters` pairs run persistently.
