@@ -50,7 +50,8 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true",
                     help="c5 only: one corr2d_compute call per problem instead of corr2d_batch")
     ap.add_argument("--n", type=int, default=0,
-                    help="c4 only: use the first N spectral variables (small profiling case)")
+                    help="small profiling cases: c4 keeps the first N spectral variables, "
+                         "c5 gives every stack N variables (same m mix)")
     ap.add_argument("--cpu-sample-n", type=int, default=0,
                     help="spectral variables of the oracle sample (0: sized to ~10-30 s)")
     return ap.parse_args()
@@ -76,6 +77,11 @@ def workload(name, precision, n_override=0):
         return dict(workload=f"hetero m=128 n1=8192 n2=2048 alpha=0.5 {precision} "
                              f"(with preprocessing)", m=128, n1=8192, n2=2048, homo=False,
                     alpha=0.5, precision=precision), raw
+    if n_override:
+        spec = wl.c5_spec(n_fixed=n_override)
+        return dict(workload=f"batched 512 problems m~U[8,200] every n={n_override} {precision}",
+                    problems=len(spec.problems), outputs=spec.total_outputs,
+                    precision=precision, alpha=0.0), spec
     spec = wl.c5_spec()
     return dict(workload=f"batched 512 problems m~U[8,200] n log-uniform [256,8192] {precision}",
                 problems=len(spec.problems), outputs=spec.total_outputs, precision=precision,

@@ -199,39 +199,51 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
     float sh = 0.f, sl = 0.f;
     float mn = __int_as_float(0x7f800000), mx = -__int_as_float(0x7f800000);
     if (valid) {
-      if (job.ref) {
-        for (int j = g; j < m; j += PREP_GROUPS) {
-          const float v = y[(long)j * ld + col];
-          mn = fminf(mn, v);
-          mx = fmaxf(mx, v);
+      if (job.ref) {  // the caller's reference: extremes only
+        for (int j0 = g; j0 < m; j0 += 32 * PREP_GROUPS) {
+          float v[32];
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int j = j0 + e * PREP_GROUPS;
+            v[e] = (j < m) ? __ldg(y + (long)j * ld + col) : 0.f;
+          }
+#pragma unroll
+          for (int e = 0; e < 32; ++e)
+            if (j0 + e * PREP_GROUPS < m) {
+              mn = fminf(mn, v[e]);
+              mx = fmaxf(mx, v[e]);
+            }
         }
       } else {
-        // Sixteen loads are in flight before the first is used.  Each four
-        // values are summed exactly as s4 + (e1 + e2 + e3) by TwoSum (the
-        // residuals are below half an ulp of s4, their FP32 sum is off by
-        // ~2^-48 s4); the pair joins the running (sh, sl) sum.
-        int j = g;
-        for (; j + 15 * PREP_GROUPS < m; j += 16 * PREP_GROUPS) {
-          float v[16];
+        // Up to 32 loads are in flight before the first is used (steps past m
+        // read as zeros: they add nothing to the sums and stay out of the
+        // extremes), so m <= 64 takes one round trip.  Each four values are
+        // summed exactly as s4 + (e1 + e2 + e3) by TwoSum (the residuals are
+        // below half an ulp of s4, their FP32 sum is off by ~2^-48 s4); the
+        // pair joins the running (sh, sl) sum.
+        for (int j0 = g; j0 < m; j0 += 32 * PREP_GROUPS) {
+          float v[32];
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[e] = __ldg(y + (long)(j + e * PREP_GROUPS) * ld + col);
+          for (int e = 0; e < 32; ++e) {
+            const int j = j0 + e * PREP_GROUPS;
+            v[e] = (j < m) ? __ldg(y + (long)j * ld + col) : 0.f;
+          }
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < 8; ++q) {
+            if (j0 + 4 * q * PREP_GROUPS >= m) break;  // warp-uniform
             const float a = v[4 * q], b = v[4 * q + 1], c = v[4 * q + 2], d = v[4 * q + 3];
             float s1, e1, s2, e2, s4, e3;
             two_sum(a, b, s1, e1);
             two_sum(c, d, s2, e2);
             two_sum(s1, s2, s4, e3);
             df_acc(sh, sl, s4, (e1 + e2) + e3);
-            mn = fminf(fminf(mn, fminf(a, b)), fminf(c, d));
-            mx = fmaxf(fmaxf(mx, fmaxf(a, b)), fmaxf(c, d));
           }
-        }
-        for (; j < m; j += PREP_GROUPS) {
-          const float v = y[(long)j * ld + col];
-          df_acc(sh, sl, v, 0.f);
-          mn = fminf(mn, v);
-          mx = fmaxf(mx, v);
+#pragma unroll
+          for (int e = 0; e < 32; ++e)
+            if (j0 + e * PREP_GROUPS < m) {
+              mn = fminf(mn, v[e]);
+              mx = fmaxf(mx, v[e]);
+            }
         }
       }
     }

@@ -73,3 +73,11 @@ def test_sample_rows_are_sorted_distinct_and_include_the_edges():
     assert np.all(np.diff(r) > 0) and r[0] == 0 and r[-1] == 999 and len(r) == 50
     assert np.array_equal(r, workloads.sample_rows(1000, 50, seed=4))
     assert np.array_equal(workloads.sample_rows(3, 10, seed=1), np.array([0, 1, 2]))
+
+
+def test_c5_fixed_n_keeps_the_m_mix():
+    full, small = workloads.c5_spec(), workloads.c5_spec(n_fixed=768)
+    assert [p.m for p in full.problems] == [p.m for p in small.problems]
+    assert [p.homo for p in full.problems] == [p.homo for p in small.problems]
+    assert all(p.n1 == p.n2 == 768 for p in small.problems)
+    assert small.total_outputs == 512 * 768 * 768

@@ -174,14 +174,18 @@ class BatchSpec:
 
 
 def c5_spec(count: int = 512, seed: int = 4, m_lo: int = 8, m_hi: int = 200,
-            n_lo: int = 256, n_hi: int = 8192) -> BatchSpec:
-    """Shapes of the batched workload: m ~ U{m_lo..m_hi}, n log-uniform, even = homo."""
+            n_lo: int = 256, n_hi: int = 8192, n_fixed: int = 0) -> BatchSpec:
+    """Shapes of the batched workload: m ~ U{m_lo..m_hi}, n log-uniform, even = homo.
+    n_fixed > 0 gives every stack n_fixed variables and keeps every other draw
+    (a smaller case with the same m mix, for profiling)."""
     rng = np.random.default_rng(seed)
     spec = BatchSpec()
     for i in range(count):
         m = int(rng.integers(m_lo, m_hi + 1))
         n1 = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
         n2r = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        if n_fixed > 0:
+            n1 = n2r = n_fixed
         homo = (i % 2 == 0)
         spec.problems.append(Problem(m, n1, n1 if homo else n2r, homo, seed * 100003 + i))
     return spec
