@@ -80,16 +80,17 @@ __device__ __forceinline__ uint32_t pack_b2(__nv_bfloat16 a, __nv_bfloat16 b) {
   return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// FP32 -> FP16 hi/lo of 8 values: hi = fp16(v), lo = fp16(v - hi).
+// FP32 -> FP16 hi/lo of 8 values: hi = fp16(v), lo = fp16(v - hi), two
+// values per conversion instruction (each rounded to nearest on its own).
 __device__ __forceinline__ void split8_f32(const float* v, uint4& hi, uint4& lo) {
   uint32_t h[4], l[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    __half h0 = __float2half_rn(v[2 * e]), h1 = __float2half_rn(v[2 * e + 1]);
-    __half l0 = __float2half_rn(v[2 * e] - __half2float(h0));
-    __half l1 = __float2half_rn(v[2 * e + 1] - __half2float(h1));
-    h[e] = pack_h2(h0, h1);
-    l[e] = pack_h2(l0, l1);
+    const __half2 hh = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
+    const float2 hf = __half22float2(hh);
+    const __half2 ll = __floats2half2_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+    h[e] = *reinterpret_cast<const uint32_t*>(&hh);
+    l[e] = *reinterpret_cast<const uint32_t*>(&ll);
   }
   hi = make_uint4(h[0], h[1], h[2], h[3]);
   lo = make_uint4(l[0], l[1], l[2], l[3]);
@@ -98,8 +99,10 @@ __device__ __forceinline__ void split8_f32(const float* v, uint4& hi, uint4& lo)
 __device__ __forceinline__ uint4 bf16x8_f32(const float* v) {
   uint32_t h[4];
 #pragma unroll
-  for (int e = 0; e < 4; ++e)
-    h[e] = pack_b2(__float2bfloat16_rn(v[2 * e]), __float2bfloat16_rn(v[2 * e + 1]));
+  for (int e = 0; e < 4; ++e) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+    h[e] = *reinterpret_cast<const uint32_t*>(&b);
+  }
   return make_uint4(h[0], h[1], h[2], h[3]);
 }
 
@@ -144,6 +147,61 @@ __device__ __forceinline__ void store_rows_chunk(uint8_t* stg, const uint4 (&pk)
       *(uint4*)((uint8_t*)(out + (size_t)(nu0 + rr) * rowlen) + c * 128 + pc * 16) = v;
   }
   __syncwarp();
+}
+
+// One centred step of the second pass: d = y - rh - rl (0 when !in_range),
+// d^2 added to the Kahan sum (ss, ss_c); returns d fy.
+__device__ __forceinline__ float center_step(float y, float2 ref, float fy, float& ss,
+                                             float& ss_c, bool in_range) {
+  float d = 0.f;
+  if (in_range) {
+    float ds, de;
+    two_sum(y, -ref.x, ds, de);
+    d = ds + (de - ref.y);
+  }
+  const float sq = fmaf(d, d, -ss_c);
+  const float tsum = ss + sq;
+  ss_c = (tsum - ss) - sq;
+  ss = tsum;
+  return d * fy;
+}
+
+// One round of the first pass over a thread's steps j0, j0 + 2, ..., j0 + 62
+// (PREP_GROUPS = 2 threads per variable): the 32 loads are in flight before
+// the first is used.  SUMS: each four values are summed exactly as
+// s4 + (e1 + e2 + e3) by TwoSum (the residuals are below half an ulp of s4,
+// their FP32 sum is off by ~2^-48 s4) and the pair joins the running (sh, sl)
+// sum.  FULL: every step is below m; otherwise the steps past m read as zeros
+// (they add nothing to the sums) and stay out of the extremes.
+template <bool FULL, bool SUMS>
+__device__ __forceinline__ void first_pass_round(const float* __restrict__ y, long ld, long col,
+                                                 int j0, int m, float& sh, float& sl, float& mn,
+                                                 float& mx) {
+  static_assert(PREP_GROUPS == 2, "step interleave of the first pass");
+  float v[32];
+#pragma unroll
+  for (int e = 0; e < 32; ++e) {
+    const int j = j0 + e * PREP_GROUPS;
+    v[e] = (FULL || j < m) ? __ldg(y + (long)j * ld + col) : 0.f;
+  }
+  if (SUMS) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (!FULL && j0 + 4 * q * PREP_GROUPS >= m) break;  // warp-uniform
+      const float a = v[4 * q], b = v[4 * q + 1], c = v[4 * q + 2], d = v[4 * q + 3];
+      float s1, e1, s2, e2, s4, e3;
+      two_sum(a, b, s1, e1);
+      two_sum(c, d, s2, e2);
+      two_sum(s1, s2, s4, e3);
+      df_acc(sh, sl, s4, (e1 + e2) + e3);
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 32; ++e)
+    if (FULL || j0 + e * PREP_GROUPS < m) {
+      mn = fminf(mn, v[e]);
+      mx = fmaxf(mx, v[e]);
+    }
 }
 
 template <int P>
@@ -192,60 +250,26 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
     tmem_relinquish();
   }
   // ---- 1. double-float partial sums over steps j = g, g+2, ..., FP32 extremes
+  // Rows past n read the last column (their results are never stored), so
+  // no load needs a row predicate.
   const float* y = job.y;
-  const long col = (long)nu * (job.cstride_m1 + 1);  // column of variable nu in y
+  const long col = (long)(valid ? nu : n - 1) * (job.cstride_m1 + 1);  // column of variable nu in y
   const long ld = job.ld;
   {
     float sh = 0.f, sl = 0.f;
     float mn = __int_as_float(0x7f800000), mx = -__int_as_float(0x7f800000);
-    if (valid) {
-      if (job.ref) {  // the caller's reference: extremes only
-        for (int j0 = g; j0 < m; j0 += 32 * PREP_GROUPS) {
-          float v[32];
-#pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const int j = j0 + e * PREP_GROUPS;
-            v[e] = (j < m) ? __ldg(y + (long)j * ld + col) : 0.f;
-          }
-#pragma unroll
-          for (int e = 0; e < 32; ++e)
-            if (j0 + e * PREP_GROUPS < m) {
-              mn = fminf(mn, v[e]);
-              mx = fmaxf(mx, v[e]);
-            }
-        }
-      } else {
-        // Up to 32 loads are in flight before the first is used (steps past m
-        // read as zeros: they add nothing to the sums and stay out of the
-        // extremes), so m <= 64 takes one round trip.  Each four values are
-        // summed exactly as s4 + (e1 + e2 + e3) by TwoSum (the residuals are
-        // below half an ulp of s4, their FP32 sum is off by ~2^-48 s4); the
-        // pair joins the running (sh, sl) sum.
-        for (int j0 = g; j0 < m; j0 += 32 * PREP_GROUPS) {
-          float v[32];
-#pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const int j = j0 + e * PREP_GROUPS;
-            v[e] = (j < m) ? __ldg(y + (long)j * ld + col) : 0.f;
-          }
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            if (j0 + 4 * q * PREP_GROUPS >= m) break;  // warp-uniform
-            const float a = v[4 * q], b = v[4 * q + 1], c = v[4 * q + 2], d = v[4 * q + 3];
-            float s1, e1, s2, e2, s4, e3;
-            two_sum(a, b, s1, e1);
-            two_sum(c, d, s2, e2);
-            two_sum(s1, s2, s4, e3);
-            df_acc(sh, sl, s4, (e1 + e2) + e3);
-          }
-#pragma unroll
-          for (int e = 0; e < 32; ++e)
-            if (j0 + e * PREP_GROUPS < m) {
-              mn = fminf(mn, v[e]);
-              mx = fmaxf(mx, v[e]);
-            }
-        }
-      }
+    // Rounds of 32 steps per thread (64 per variable) with every step below
+    // m run without predicates; the last, partial round reads the steps past
+    // m as zeros.
+    int j0 = g;
+    if (job.ref) {  // the caller's reference: extremes only
+      for (; j0 + 31 * PREP_GROUPS < m; j0 += 32 * PREP_GROUPS)
+        first_pass_round<true, false>(y, ld, col, j0, m, sh, sl, mn, mx);
+      if (j0 < m) first_pass_round<false, false>(y, ld, col, j0, m, sh, sl, mn, mx);
+    } else {
+      for (; j0 + 31 * PREP_GROUPS < m; j0 += 32 * PREP_GROUPS)
+        first_pass_round<true, true>(y, ld, col, j0, m, sh, sl, mn, mx);
+      if (j0 < m) first_pass_round<false, true>(y, ld, col, j0, m, sh, sl, mn, mx);
     }
     red_sh[g * PREP_ROWS + r] = sh;
     red_sl[g * PREP_ROWS + r] = sl;
@@ -257,7 +281,7 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
   tc_fence_after();
   if (g == 0) {
     float rh = 0.f, rl = 0.f, amax = 0.f;
-    if (valid) {
+    {  // rows past n repeat the last variable
       float mn = red_mn[r], mx = red_mx[r];
       float sh = red_sh[r], sl = red_sl[r];
       for (int k = 1; k < PREP_GROUPS; ++k) {
@@ -304,14 +328,20 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
   for (int kc = 0; kc < jchunks; ++kc) {
     // this thread's groups of 8 steps: jg = g, g + 2, g + 4, g + 6; the loads
     // are issued before waiting for the previous chunk's MMAs
+    // (groups of 8 steps below m load without predicates; warp-uniform)
     float yv[PREP_JG][8];
 #pragma unroll
-    for (int h = 0; h < PREP_JG; ++h)
+    for (int h = 0; h < PREP_JG; ++h) {
+      const int jb = kc * 64 + (g + PREP_GROUPS * h) * 8;
+      if (jb + 8 <= m) {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int j = kc * 64 + (g + PREP_GROUPS * h) * 8 + e;
-        yv[h][e] = (valid && j < m) ? __ldg(y + (long)j * ld + col) : 0.f;
+        for (int e = 0; e < 8; ++e) yv[h][e] = __ldg(y + (long)(jb + e) * ld + col);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          yv[h][e] = (jb + e < m) ? __ldg(y + (long)(jb + e) * ld + col) : 0.f;
       }
+    }
     if (kc > 0) ok = ok && mbar_wait(mbar, (kc - 1) & 1, wc);  // smem free again
     if (t == 0 && ok) {
       mbar_arrive_expect_tx(wbar, P * wbytes);
@@ -330,22 +360,15 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
         if (P == 2) *(uint4*)(sA + PREP_ROWS * 128 + off) = z;
         continue;
       }
+      // centering y - rh - rl (steps past m: 0); scaling by 2^ey is exact
       float v[8];
+      if (kc * 64 + jg * 8 + 8 <= m) {  // warp-uniform
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int j = kc * 64 + jg * 8 + e;
-        // centering y - rh - rl; scaling by 2^ey is exact
-        float d = 0.f;
-        if (valid && j < m) {
-          float ds, de;
-          two_sum(yv[h][e], -ref.x, ds, de);
-          d = ds + (de - ref.y);
-        }
-        const float sq = fmaf(d, d, -ss_c);
-        const float tsum = ss + sq;
-        ss_c = (tsum - ss) - sq;
-        ss = tsum;
-        v[e] = d * fy;
+        for (int e = 0; e < 8; ++e) v[e] = center_step(yv[h][e], ref, fy, ss, ss_c, true);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          v[e] = center_step(yv[h][e], ref, fy, ss, ss_c, kc * 64 + jg * 8 + e < m);
       }
       if (P == 2) {
         uint4 hi, lo;
@@ -417,6 +440,12 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
   const int nch = kp / gsz;
   uint8_t* stg = base + warp * 4096;  // the operand tiles are free after the last MMA
   const int nu0 = item.tile * PREP_ROWS + q * 32;
+  // The half-spectrum weight w (1 at omega = 0, the first element of chunk
+  // 0; 2 otherwise) enters both operands as sqrt(w), so that every product
+  // of a stack-1 and a stack-2 row carries w and a homo problem needs one row
+  // set for both.  The Hilbert variant has weight 1 everywhere.  fY is a
+  // power of two, so one product by fY sqrt(w) rounds as (x fY) sqrt(w) does.
+  const float fYw = job.plain_weights ? fY : fY * 1.41421356f;
   for (int c = part; c < nch; c += PREP_GROUPS) {
     float re[32], im[32];
     if (P == 2) {
@@ -424,26 +453,15 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
       tmem_ld16(trow + c * 16, a);
       tmem_ld16(trow + kp + c * 16, b);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) { re[i] = a[i] * fY; im[i] = b[i] * fY; }
+      for (int i = 0; i < 16; ++i) { re[i] = a[i] * fYw; im[i] = b[i] * fYw; }
+      if (c == 0) { re[0] = a[0] * fY; im[0] = b[0] * fY; }
     } else {
       float a[32], b[32];
       tmem_ld32(trow + c * 32, a);
       tmem_ld32(trow + kp + c * 32, b);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) { re[i] = a[i] * fY; im[i] = b[i] * fY; }
-    }
-    // The half-spectrum weight w (1 at omega = 0, the first element of chunk
-    // 0; 2 otherwise) enters both operands as sqrt(w), so that every product
-    // of a stack-1 and a stack-2 row carries w and a homo problem needs one
-    // row set for both.  The Hilbert variant has weight 1 everywhere.
-    if (!job.plain_weights) {
-      const float rt2 = 1.41421356f;
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const float f = (c == 0 && i == 0) ? 1.f : rt2;
-        re[i] *= f;
-        im[i] *= f;
-      }
+      for (int i = 0; i < 32; ++i) { re[i] = a[i] * fYw; im[i] = b[i] * fYw; }
+      if (c == 0) { re[0] = a[0] * fY; im[0] = b[0] * fY; }
     }
     uint4 pk[8];
     pack_chunk<P>(re, im, pk);

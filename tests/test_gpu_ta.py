@@ -202,3 +202,42 @@ def test_ta_stalled_producer_times_out_and_context_survives():
         assert ok.kernel_info()[0] == pkg.XSPEC_TC_TA
         ophi, opsi, _, _ = oracle.corr2d(y.cpu().numpy())
         check(host(phi), host(psi), ophi, opsi, 1e-5, "after time-out")
+
+
+def _oracle_hilbert(y1, y2=None, alpha=0.0):
+    d1 = oracle.dynamic(y1, oracle.reference_mean(y1))
+    d2 = d1 if y2 is None else oracle.dynamic(y2, oracle.reference_mean(y2))
+    phi, psi = oracle.hilbert_noda(d1, d2)
+    if alpha > 0:
+        s1 = np.array([oracle.scale_factor(s, alpha) for s in oracle.sigma(d1)])
+        s2 = np.array([oracle.scale_factor(s, alpha) for s in oracle.sigma(d2)])
+        phi, psi = phi * np.outer(s1, s2), psi * np.outer(s1, s2)
+    return phi, psi
+
+
+@pytest.mark.parametrize("m,n1,n2", [(16, 300, None), (100, 260, None), (40, 333, 170)])
+def test_ta_runs_the_hilbert_variant_when_forced(ctx, m, n1, n2):
+    """The Hilbert-transform operands (two row sets even for homo problems, up
+    to 8 chunks of 16 steps) through the TMEM-operand kernel."""
+    y1 = workloads.random_stack(m, n1, seed=2900 + m, offset=2.0)
+    y2 = None if n2 is None else workloads.random_stack(m, n2, seed=2950 + m, offset=-1.0)
+    alpha = 0.0 if n2 is None else 0.5
+    phi, psi = run(ctx, y1, y2, tiles="128:0:0:1:3", hilbert=True, alpha=alpha)
+    ophi, opsi = _oracle_hilbert(y1, y2, alpha=alpha)
+    assert rel(phi, ophi) < 1e-5
+    assert np.abs(psi - opsi).max() <= 1e-5 * np.abs(ophi).max()
+
+
+def test_ta_row_slabs_use_the_single_cta_kernel(ctx):
+    """A row slab is not a whole problem: the single-CTA kernel computes it,
+    and its rows equal those of the whole map."""
+    import paper_1808_00685_gb300 as pkg
+    y = workloads.random_stack(64, 700, seed=3000)
+    full = run(ctx, y, no_mirror=True)
+    with _Env(CORR2D_XSPEC="ta", CORR2D_TILES=None):
+        phi, psi = ctx.compute_rows(dev(y), None, 256, 300)
+        ctx.synchronize()
+    assert ctx.kernel_info()[0] == pkg.XSPEC_TC
+    ophi, opsi, _, _ = oracle.corr2d(y)
+    check(host(phi), host(psi), ophi[256:556], opsi[256:556], 1e-5, "ta row slab")
+    assert np.abs(host(phi) - full[0][256:556]).max() <= 1e-6 * np.abs(full[0]).max()
