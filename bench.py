@@ -325,37 +325,49 @@ def run_ours(args, world, rank, local, pg):
         desc["batched"] = not (args.no_batch or args.precision == "fp32")
         y = None
 
-    ctx.set_profiling(True)
-    for _ in range(max(args.warmup, 0)):
-        step()
-    ctx.synchronize()
-    torch.cuda.synchronize()
-    kind, pair_clusters = ctx.kernel_info()
-    kernel = {pkg.XSPEC_TC: "k_xspec_tc", pkg.XSPEC_TC_PAIR: "k_xspec_pair",
-              pkg.XSPEC_TC_TA: "k_xspec_ta",
-              pkg.XSPEC_FP32: "k_xspec_simt"}.get(kind, "none")
-    barrier(pg)
-
+    # The clock sampler starts (and settles) before the warm-up, so that the GPU
+    # is not left idle between the warm-up and the timed steps.
     sampler = ClockSampler(local)
     sampler.start()
-    torch.cuda.synchronize()
-    barrier(pg)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    r0.record(stream)
-    prep_ms, xspec_ms = [], []
-    for k in range(args.steps):
-        flush.zero_()  # L2 flush, outside the step's events
-        ev[k][0].record(stream)
-        step()
-        ev[k][1].record(stream)
-        p_ms, x_ms = ctx.timings()  # waits for this step's kernel events
-        prep_ms.append(p_ms)
-        xspec_ms.append(x_ms)
-    r1.record(stream)
-    torch.cuda.synchronize()
-    barrier(pg)
+    try:
+        ctx.set_profiling(True)
+        # warm-up steps run exactly like the timed ones (flush, events, step,
+        # per-kernel timings), so that no first-use cost lands in a timed step
+        for _ in range(max(args.warmup, 0)):
+            flush.zero_()
+            w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            w0.record(stream)
+            step()
+            w1.record(stream)
+            ctx.timings()
+            w1.synchronize()
+        ctx.synchronize()
+        torch.cuda.synchronize()
+        kind, pair_clusters = ctx.kernel_info()
+        kernel = {pkg.XSPEC_TC: "k_xspec_tc", pkg.XSPEC_TC_PAIR: "k_xspec_pair",
+                  pkg.XSPEC_TC_TA: "k_xspec_ta",
+                  pkg.XSPEC_FP32: "k_xspec_simt"}.get(kind, "none")
+        barrier(pg)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        prep_ms, xspec_ms = [], []
+        for k in range(args.steps):
+            flush.zero_()  # L2 flush, outside the step's events
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            p_ms, x_ms = ctx.timings()  # waits for this step's kernel events
+            prep_ms.append(p_ms)
+            xspec_ms.append(x_ms)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        barrier(pg)
+    except BaseException:
+        sampler.stop()  # no nvidia-smi left running
+        raise
     clocks = sampler.stop()
     ctx.synchronize()  # raises on a device-side time-out
     step_ms = [a.elapsed_time(b) for a, b in ev]
