@@ -211,9 +211,11 @@ corr2d_status corr2d_interpolate_perturbation(corr2d_ctx* ctx, int method, int m
  * tile choice on the caller's buffers: each candidate (mirrored or full tiles,
  * tile order) runs three times and the fastest cross-spectrum launch wins;
  * later calls reuse it.  CORR2D_NO_TUNE=1 takes the first candidate;
- * CORR2D_TILES=bn:mirror:group:chunk forces one choice (bn 64 or 128, mirror
- * 0/1, group 0 for row-major or G for G x G super-blocks, chunk >= 1 list
- * entries per CTA at a time).  Repeated calls with the same buffers and
+ * CORR2D_TILES=bn:mirror:group:chunk[:seg] forces one choice (bn 64 or 128,
+ * mirror 0/1, group 0 for row-major or G for G x G super-blocks, chunk >= 1
+ * list entries per CTA at a time; seg > 0 runs the kernel that keeps the
+ * stack-1 operand in TMEM, on row segments of seg 128 x 128 tiles, when the
+ * problem has at most 8 frequency chunks).  Repeated calls with the same buffers and
  * arguments (up to four recent sets) launch from descriptors already on the
  * device.  The launches use the context's workspace, which a later call with
  * other shapes may reallocate: do not capture corr2d_compute into a CUDA
