@@ -47,7 +47,8 @@ struct TileChoice {
   int group = 0;  // tile order: 0 row-major, G > 0: G x G tile super-blocks
   int pair = 0;   // 1: CTA-pair kernel (256 x 128 items, bn = 128)
   int chunk = 1;  // consecutive list entries each CTA takes at a time
-  int ta = 0;     // > 0: TMEM-operand kernel (128 x 64 tiles), row segments of ta tiles
+  int ta = 0;     // > 0: TMEM-operand kernel (128 x 128 tiles), row segments of ta tiles
+  int stages = 4; // operand stages in flight in the single-CTA kernel (4 or 5)
 };
 
 // Device descriptors of the last corr2d_compute call and the arguments they
@@ -60,6 +61,7 @@ struct LaunchPlan {
   bool pair = false;  // cross-spectrum on CTA pairs
   bool ta = false;    // cross-spectrum with the stack-1 operand in TMEM (XSeg list)
   int chunk = 1;      // run length of list entries per CTA
+  int stages = 4;     // operand stages of the single-CTA kernel
 };
 
 // A recently used corr2d_compute launch: its key, descriptor offsets and the
@@ -440,7 +442,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
       CUDA_TRY(ctx, launch_xspec_tc((const XProblem*)(d + lp.off_probs),
                                     (const XItem*)(d + lp.off_xitems), lp.nxitems, lp.planes,
                                     ctx->sm_count, ctx->d_err, ctx->limit_ns, ctx->stream,
-                                    ctx->fault_inject, lp.chunk));
+                                    ctx->fault_inject, lp.chunk, lp.stages));
     if (ctx->profiling) {
       cudaEventRecord(ctx->ev[2], ctx->stream);
       ctx->recorded = true;
@@ -459,7 +461,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
     const void* ptrs[] = {y1, y2, phi, psi, sig1, sig2, p.ref1, p.ref2, opsbuf.p};
     const int ints[] = {m, n1, ld1, n2, ld2, out_rows, p.ref_mode, p.precision, (int)p.flags,
                         tc.bn, tc.mirror, tc.group, ti_begin, ti_end, out_row_tile0,
-                        skip_prep ? 1 : 0, cstride, tc.pair, tc.chunk, tc.ta};
+                        skip_prep ? 1 : 0, cstride, tc.pair, tc.chunk, tc.ta, tc.stages};
     put(ptrs, sizeof ptrs);
     put(ints, sizeof ints);
     put(&ldo, sizeof ldo);
@@ -562,6 +564,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   lp.pair = pair;
   lp.ta = ta;
   lp.chunk = (pair || ta) ? 1 : std::max(1, tc.chunk);
+  lp.stages = tc.stages == 5 ? 5 : 4;
   if (slot) {
     slot->plan = lp;
     slot->plan.key = key;
@@ -939,19 +942,22 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
                              flag_bits + 16 * p.precision +
                                  256 * ((want_pair ? 1 : 0) + (want_single ? 2 : 0) +
                                         (want_ta ? 4 : 0)));
-  // CORR2D_TILES=bn:mirror:group:chunk[:seg] forces one tile choice (tests of
-  // every order; seg > 0 selects the TMEM-operand kernel); it is not cached
+  // CORR2D_TILES=bn:mirror:group:chunk[:seg[:stages]] forces one tile choice
+  // (tests of every order; seg > 0 selects the TMEM-operand kernel, stages 4
+  // or 5 the single-CTA kernel's operand ring); it is not cached
   if (const char* ft = getenv("CORR2D_TILES")) {
     TileChoice c;
-    const int nf = sscanf(ft, "%d:%d:%d:%d:%d", &c.bn, &c.mirror, &c.group, &c.chunk, &c.ta);
-    if ((nf == 4 || nf == 5) && (c.bn == 64 || c.bn == 128) && c.group >= 0 && c.chunk >= 1 &&
-        c.ta >= 0 && c.ta <= 4096) {
+    const int nf = sscanf(ft, "%d:%d:%d:%d:%d:%d", &c.bn, &c.mirror, &c.group, &c.chunk, &c.ta,
+                          &c.stages);
+    if (nf >= 4 && (c.bn == 64 || c.bn == 128) && c.group >= 0 && c.chunk >= 1 && c.ta >= 0 &&
+        c.ta <= 4096 && (c.stages == 4 || c.stages == 5)) {
       if (!homo || (p.flags & CORR2D_FLAG_NO_MIRROR)) c.mirror = 0;
       *out = c;
       return CORR2D_OK;
     }
     return fail(ctx, CORR2D_EINVAL,
-                "CORR2D_TILES must be bn:mirror:group:chunk[:seg] (bn 64 or 128, seg 0..4096)");
+                "CORR2D_TILES must be bn:mirror:group:chunk[:seg[:stages]] (bn 64 or 128, seg "
+                "0..4096, stages 4 or 5)");
   }
   auto it = ctx->tuned.find(key);
   if (it != ctx->tuned.end()) { *out = it->second; return CORR2D_OK; }
@@ -981,8 +987,12 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
       cands.push_back(TileChoice{128, 0, 12, 1});
     }
     if (want_single) {
-      cands.push_back(TileChoice{128, 0, 0});
-      cands.push_back(TileChoice{128, 0, 12});
+      // (a fifth operand stage helps full tiles: homo m = 64 n = 32768 1.29 ->
+      // 1.22 ms; mirrored ones it slows: c4 1.35 -> 1.39 ms)
+      for (int st : {4, 5}) {
+        cands.push_back(TileChoice{128, 0, 0, 0, 1, 0, st});
+        cands.push_back(TileChoice{128, 0, 12, 0, 1, 0, st});
+      }
       cands.push_back(TileChoice{64, 0, 0});
     }
     if (want_ta)
@@ -1025,9 +1035,9 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
   size_t bi = 0;
   for (size_t i = 0; i < cands.size(); ++i) {
     if (getenv("CORR2D_VERBOSE"))
-      fprintf(stderr, "corr2d tuner m=%d n1=%d n2=%d: bn=%d mirror=%d group=%d chunk=%d pair=%d seg=%d -> %.4f ms\n",
+      fprintf(stderr, "corr2d tuner m=%d n1=%d n2=%d: bn=%d mirror=%d group=%d chunk=%d pair=%d seg=%d stages=%d -> %.4f ms\n",
               m, n1, n2e, cands[i].bn, cands[i].mirror, cands[i].group, cands[i].chunk,
-              cands[i].pair, cands[i].ta, best_ms[i]);
+              cands[i].pair, cands[i].ta, cands[i].stages, best_ms[i]);
     if (best_ms[i] < best_ms[bi]) bi = i;
   }
   ctx->tuned[key] = cands[bi];

@@ -124,13 +124,13 @@ cudaError_t launch_prep_tc(const PrepJob* d_jobs, const PrepItem* d_items, int n
                            int max_kp, int* err, unsigned long long limit_ns, cudaStream_t s);
 // inject & 1 makes the producer issue nothing (host-requested fault for the
 // time-out test); 0 in normal operation.  Each CTA takes runs of `chunk`
-// consecutive work items.
+// consecutive work items; `stages` (4 or 5) operand stages are in flight.
 cudaError_t launch_xspec_tc(const XProblem* d_probs, const XItem* d_items, int nitems,
                             int planes, int grid, int* err, unsigned long long limit_ns,
-                            cudaStream_t s, int inject = 0, int chunk = 1);
+                            cudaStream_t s, int inject = 0, int chunk = 1, int stages = 4);
 
 // Row segment of the TMEM-operand cross-spectrum kernel: tiles (ti, tj0 ..
-// tj0 + ntj - 1) of 128 x 64 outputs that share their stack-1 rows.
+// tj0 + ntj - 1) of 128 x 128 outputs that share their stack-1 rows.
 struct XSeg {
   int prob;
   uint16_t ti, tj0, ntj, pad_;

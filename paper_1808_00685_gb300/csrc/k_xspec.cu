@@ -8,7 +8,8 @@
 //
 // Persistent, warp-specialised kernel, one CTA per SM, 320 threads:
 //   warp 0      TMA producer: operand chunks of stack 1 (128 rows) and
-//               stack 2 (bn rows) into a 4-stage shared-memory ring
+//               stack 2 (bn rows) into a shared-memory ring of 4 or 5
+//               stages (the tuner's choice: 5 helps full tiles, 4 mirrored)
 //   warp 1      MMA issuer (one thread): per chunk, Phi and Psi accumulate in
 //               TMEM (128 lanes x bn columns each); the Re*Im term of Psi
 //               uses the instruction's negate-A bit.  With FP16 hi/lo planes
@@ -28,7 +29,7 @@
 
 namespace c2d {
 
-constexpr int XS_STAGES = 4;
+constexpr int XS_STAGES = 5;  // ring slots allocated; a launch uses 4 or 5 of them
 constexpr int XS_STAGE_BYTES = 2 * TILE_M * 128;  // A chunk + B chunk (bn <= 128 rows)
 constexpr int XS_EPI_WARPS = 8;
 constexpr int XS_BOX_BYTES = 32 * 32 * 4;
@@ -37,7 +38,7 @@ static_assert(XS_EPI_SLOTS >= 2, "a box and its mirror need two staging slots");
 constexpr int XS_THREADS = 64 + 32 * XS_EPI_WARPS;
 constexpr size_t XS_SMEM = 1024 + (size_t)XS_STAGES * XS_STAGE_BYTES +
                            (size_t)XS_EPI_WARPS * XS_EPI_SLOTS * XS_BOX_BYTES +
-                           (size_t)XS_EPI_WARPS * TILE_N * 4 + 256;
+                           (size_t)2 * TILE_N * 4 + 256;
 
 // Accumulation order.  Tensor-core FP32 accumulation truncates each addition,
 // so its error grows with the number of MMAs added while the accumulator is
@@ -87,13 +88,13 @@ __device__ __forceinline__ int item_at(int k, int chunk) {
 template <int P>
 __global__ void __launch_bounds__(XS_THREADS, 1)
     k_xspec_tc(const XProblem* __restrict__ probs, const XItem* __restrict__ items, int nitems,
-               int* err, unsigned long long limit_ns, int inject, int chunk) {
+               int* err, unsigned long long limit_ns, int inject, int chunk, int nst) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* stages = base;
   uint8_t* epi = base + XS_STAGES * XS_STAGE_BYTES;
   float* s2stage = (float*)(epi + XS_EPI_WARPS * XS_EPI_SLOTS * XS_BOX_BYTES);
-  uint64_t* bars = (uint64_t*)(s2stage + XS_EPI_WARPS * TILE_N);
+  uint64_t* bars = (uint64_t*)(s2stage + 2 * TILE_N);
   // bars: full[S], empty[S], tfull[2], tempty[2]
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * XS_STAGES + 4);
   auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
           const int cx = (nch - 1 - c) * CHUNK_ELEMS;  // high frequencies first
           tma_load_2d_hint(sa, &pr->tmA, cx, (int)w.ti * TILE_M, full_bar(stage), keep);
           tma_load_2d_hint(sa + TILE_M * 128, &pr->tmB, cx, (int)w.tj * bn, full_bar(stage), keep);
-          if (++stage == XS_STAGES) { stage = 0; phase ^= 1u; }
+          if (++stage == nst) { stage = 0; phase ^= 1u; }
         }
       }
       // every load this thread started has landed before shared memory is released
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
           ++committed;
           last_bar = empty_bar(stage);
           last_parity = phase;
-          if (++stage == XS_STAGES) { stage = 0; phase ^= 1u; }
+          if (++stage == nst) { stage = 0; phase ^= 1u; }
         }
         if (!ok) break;
         mma_commit(tfull_bar(buf));
@@ -225,7 +226,6 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
     const float sg = half ? -1.f : 1.f;
     const uint64_t stream_out = l2_policy_evict_first();  // written once, never re-read here
     uint8_t* ring = epi + ew * XS_EPI_SLOTS * XS_BOX_BYTES;
-    float* s2w = s2stage + ew * TILE_N;
     int lt = 0;
     int slot = 0;  // next slot of this warp's staging ring
     int cur_prob = -1;
@@ -257,9 +257,13 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
       const int colt = (int)w.tj * bn;                // first nu2 of the tile
       // tile constants while the MMAs finish: row scale, column scales in smem
       const float rs = (row < n1) ? norm * __ldg(s1p + row) : 0.f;
+      // column scales of the tile, loaded while the MMAs finish; stored into
+      // the tile-parity half of the buffer all epilogue warps share once the
+      // accumulators are ready (every warp has then left the tile two back,
+      // the last one to use that half; all warps store the same values)
+      float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
       {
         const int c = colt + lane * 4;
-        float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
         if (lane * 4 < bn) {
           if (c + 3 < n2) {
             sv = __ldg((const float4*)(s2p + c));
@@ -268,7 +272,6 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
             if (c + 1 < n2) sv.y = __ldg(s2p + c + 1);
             if (c + 2 < n2) sv.z = __ldg(s2p + c + 2);
           }
-          *(float4*)(s2w + lane * 4) = sv;
         }
       }
       __syncwarp();
@@ -276,6 +279,9 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
       const uint32_t tpar = (uint32_t)(lt >> 1) & 1u;
       if (!mbar_wait(tfull_bar(buf), tpar, wc)) break;
       tc_fence_after();
+      float* s2w = s2stage + (lt & 1) * TILE_N;
+      if (lane * 4 < bn) *(float4*)(s2w + lane * 4) = sv;
+      __syncwarp();
       // Homo tiles off the diagonal store each box and its mirror.  On a
       // diagonal tile, box (q, cc) with cc > q stores itself and its mirror,
       // cc == q stores its upper triangle and mirrors it into the lower one,
@@ -374,16 +380,17 @@ cudaError_t init_xspec_kernels() {
 
 cudaError_t launch_xspec_tc(const XProblem* d_probs, const XItem* d_items, int nitems, int planes,
                             int grid, int* err, unsigned long long limit_ns, cudaStream_t s,
-                            int inject, int chunk) {
+                            int inject, int chunk, int stages) {
   if (nitems <= 0) return cudaSuccess;
   if (chunk < 1) chunk = 1;
+  if (stages != XS_STAGES) stages = 4;
   if ((long)grid * chunk > nitems) grid = (nitems + chunk - 1) / chunk;
   if (planes == 2)
     k_xspec_tc<2><<<grid, XS_THREADS, XS_SMEM, s>>>(d_probs, d_items, nitems, err, limit_ns, inject,
-                                                    chunk);
+                                                    chunk, stages);
   else
     k_xspec_tc<1><<<grid, XS_THREADS, XS_SMEM, s>>>(d_probs, d_items, nitems, err, limit_ns, inject,
-                                                    chunk);
+                                                    chunk, stages);
   return cudaGetLastError();
 }
 

@@ -271,7 +271,9 @@ def test_plan_cache_cycles_through_more_buffer_sets_than_slots(ctx):
 
 @pytest.mark.parametrize("tiles", ["128:1:0:1", "128:1:8:1", "128:1:12:1", "128:1:16:1",
                                    "128:1:24:1", "128:1:32:1", "128:1:64:1", "128:1:96:1",
-                                   "128:1:8:4", "128:0:0:1", "128:0:12:1", "64:0:0:1"])
+                                   "128:1:8:4", "128:0:0:1", "128:0:12:1", "64:0:0:1",
+                                   "128:0:0:1:0:5", "128:0:12:1:0:5", "128:1:64:1:0:5",
+                                   "128:1:8:4:0:5"])
 def test_every_tile_order_gives_the_oracle_result(ctx, tiles):
     """Each tile choice the tuner may pick (width, mirror, order: row-major or
     G x G super-blocks; run length per CTA), forced through CORR2D_TILES, on
