@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 import workloads
+import test_oracle_pins as pins
 from test_oracle_pins import _brute, _dense_fmm_spline, _grid, _rel
 
 MUTATIONS = {
@@ -43,6 +44,49 @@ MUTATIONS = {
                                   "rhs[m - 1] = g1 * (time[m - 2] - time[m - 3]);"),
     "spline_eval_weight": ("(yv[seg] - M[seg] * h * h / 6.0) * A / h",
                            "(yv[seg] - M[seg] * h * h / 6.0) * B / h"),
+    "dyn_out_ref_sign": ("dyn_out[(long)j * n_out + k] = val - (ref ? (double)ref[k] : 0.0);",
+                         "dyn_out[(long)j * n_out + k] = val + (ref ? (double)ref[k] : 0.0);"),
+    "hilbert_pi_dropped": ("if (k != j) s += d2[(long)k * n2 + b] / (ORACLE_PI * (double)(k - j));",
+                           "if (k != j) s += d2[(long)k * n2 + b] / ((double)(k - j));"),
+    "hilbert_transposed": ("if (k != j) s += d2[(long)k * n2 + b] / (ORACLE_PI * (double)(k - j));",
+                           "if (k != j) s += d2[(long)k * n2 + b] / (ORACLE_PI * (double)(j - k));"),
+    "hilbert_psi_over_m": ("psi[(long)a * n2 + b] = sq / (double)(m - 1);",
+                           "psi[(long)a * n2 + b] = sq / (double)m;"),
+    "hilbert_phi_over_m": ("phi[(long)a * n2 + b] = sp / (double)(m - 1);",
+                           "phi[(long)a * n2 + b] = sp / (double)m;"),
+    "hilbert_on_stack_1": (
+        """  double* z = malloc(sizeof(double) * (size_t)m * n2);
+  if (!z) return;
+  for (int b = 0; b < n2; ++b)
+    for (int j = 0; j < m; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k)
+        if (k != j) s += d2[(long)k * n2 + b] / (ORACLE_PI * (double)(k - j));
+      z[(long)j * n2 + b] = s;
+    }
+  for (int a = 0; a < n1; ++a)
+    for (int b = 0; b < n2; ++b) {
+      double sp = 0.0, sq = 0.0;
+      for (int j = 0; j < m; ++j) {
+        sp += d1[(long)j * n1 + a] * d2[(long)j * n2 + b];
+        sq += d1[(long)j * n1 + a] * z[(long)j * n2 + b];
+      }""",
+        """  double* z = malloc(sizeof(double) * (size_t)m * n1);
+  if (!z) return;
+  for (int a = 0; a < n1; ++a)
+    for (int j = 0; j < m; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k)
+        if (k != j) s += d1[(long)k * n1 + a] / (ORACLE_PI * (double)(k - j));
+      z[(long)j * n1 + a] = s;
+    }
+  for (int a = 0; a < n1; ++a)
+    for (int b = 0; b < n2; ++b) {
+      double sp = 0.0, sq = 0.0;
+      for (int j = 0; j < m; ++j) {
+        sp += d1[(long)j * n1 + a] * d2[(long)j * n2 + b];
+        sq += z[(long)j * n1 + a] * d2[(long)j * n2 + b];
+      }"""),
 }
 
 
@@ -139,12 +183,36 @@ def _battery():
         return all(np.allclose(out[:, v], _dense_fmm_spline(t, yy[:, v].astype(np.float64), g),
                                atol=1e-9) for v in range(2))
 
+    def interp_dyn_out():
+        pins.test_interp_dyn_out_is_the_dynamic_spectrum_of_the_correlation()
+        return True
+
+    def hilbert_by_hand():
+        for m in (3, 4):
+            pins.test_hilbert_noda_matrix_written_out_by_hand(m)
+        return True
+
+    def hilbert_hetero():
+        pins.test_hilbert_noda_hetero_applies_the_matrix_to_stack_2()
+        return True
+
+    def hilbert_sinusoid():
+        pins.test_hilbert_noda_of_a_sinusoid_is_the_cosine_times_the_kernel_gain(0.7)
+        return True
+
+    def ft_ht_tone():
+        pins.test_ft_and_ht_async_spectra_agree_on_a_single_tone(513, 20)
+        return True
+
     for name, fn in [("brute_homo", brute_homo), ("brute_hetero_odd", brute_hetero_odd),
                      ("brute_user_ref", brute_user_ref), ("parseval_even", parseval_even),
                      ("pearson_diag", pearson_diag), ("closed_form", closed_form),
                      ("dft_numpy", dft_numpy), ("sigma_numpy", sigma_numpy),
                      ("interp_numpy", interp_numpy), ("interp_t_numpy", interp_t_numpy),
-                     ("spline_cubic", spline_cubic), ("spline_dense", spline_dense)]:
+                     ("spline_cubic", spline_cubic), ("spline_dense", spline_dense),
+                     ("interp_dyn_out", interp_dyn_out), ("hilbert_by_hand", hilbert_by_hand),
+                     ("hilbert_hetero", hilbert_hetero), ("hilbert_sinusoid", hilbert_sinusoid),
+                     ("ft_ht_tone", ft_ht_tone)]:
         check(name, fn)
     return failed
 

@@ -6,9 +6,35 @@ closed form for sinusoidal bands, an exact invariance, the Noda sign rules or
 the R index expression of the paper's FFT snippet).  A dropped term, a wrong
 sign or index, a transposed operand or a wrong weight in the oracle fails at
 least one of them.
+
+The pins of each oracle function (``oracle/__init__.py``):
+
+  num_freq, weight          test_kept_frequencies_follow_r_index_expression,
+                            test_parseval_links_frequency_sum_to_covariance
+  default_norm              test_pearson_diagonal_is_m_over_pi_for_odd_m,
+                            test_closed_form_sinusoidal_bands, test_norm_override_and_constant_variable
+  scale_factor, sigma       test_reference_and_sigma_match_numpy, test_amplitude_scaling,
+                            test_norm_override_and_constant_variable
+  reference_mean, dynamic   test_reference_and_sigma_match_numpy, test_baseline_offset_invariance
+  dft                       test_dft_is_numpy_fft_truncated
+  cross_spectrum, corr2d    test_brute_force_*, test_parseval_*, test_closed_form_*,
+                            test_fig1_*, the invariance tests, test_noda_sign_rules_*,
+                            test_row_subset_matches_full, test_sampled_columns_give_those_entries
+  interp_linear (y_out)     test_interp_matches_numpy_interp_and_endpoints,
+                            test_interp_reproduces_linear_functions_and_subtracts_reference
+  interp_linear (dyn_out)   test_interp_dyn_out_is_the_dynamic_spectrum_of_the_correlation
+  interp_perturbation       test_perturbation_interp_* (linear), test_spline_* (spline)
+  reduce_map                test_reduce_map_is_decimation
+  hilbert_noda              test_hilbert_noda_matrix_written_out_by_hand,
+                            test_hilbert_noda_hetero_applies_the_matrix_to_stack_2,
+                            test_hilbert_noda_of_a_sinusoid_is_the_cosine_times_the_kernel_gain,
+                            test_ft_and_ht_async_spectra_agree_on_a_single_tone,
+                            test_odd_m_ft_equals_ht_synchronous_up_to_m_over_pi,
+                            test_hilbert_noda_async_sign_agrees_with_ft
 """
 import math
 import os
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -389,6 +415,102 @@ def test_hilbert_noda_async_sign_agrees_with_ft():
     assert np.sign(hpsi[45, 15]) == np.sign(psi[45, 15]) == 1.0
 
 
+# Eq. HilbNoda worked out by hand for m = 3 and m = 4: the entries of pi * N
+# (row j, column k), pi N_jk = 1/(k - j) off the diagonal, 0 on it.
+_F = Fraction
+_PI_TIMES_N = {
+    3: [[_F(0), _F(1), _F(1, 2)],
+        [_F(-1), _F(0), _F(1)],
+        [_F(-1, 2), _F(-1), _F(0)]],
+    4: [[_F(0), _F(1), _F(1, 2), _F(1, 3)],
+        [_F(-1), _F(0), _F(1), _F(1, 2)],
+        [_F(-1, 2), _F(-1), _F(0), _F(1)],
+        [_F(-1, 3), _F(-1, 2), _F(-1), _F(0)]],
+}
+
+
+@pytest.mark.parametrize("m", [3, 4])
+def test_hilbert_noda_matrix_written_out_by_hand(m):
+    """Unit-impulse dynamic spectra pick single terms of Eqs. disHTsyn, disHT and
+    disHTasyn: with d1 = d2 = the m x m identity (variable a is an impulse at step a),
+    (m - 1) Phi = I and (m - 1) Psi[a, b] = sum_j d1(j, a) sum_k N_jk d2(k, b) = N_ab.
+    Pins the 1/pi of Eq. HilbNoda, the 1/(m - 1) of both spectra and the orientation
+    of N (a transposed N, or N applied to stack 1, flips every sign)."""
+    eye = np.eye(m)
+    phi, psi = oracle.hilbert_noda(eye, eye)
+    assert np.array_equal((m - 1) * phi, eye)
+    pin = np.array([[float(v) for v in row] for row in _PI_TIMES_N[m]])
+    assert np.max(np.abs(math.pi * (m - 1) * psi - pin)) < 1e-14
+
+
+def test_hilbert_noda_hetero_applies_the_matrix_to_stack_2():
+    """Hetero Eq. disHTasyn: Psi = d1^T (N d2) / (m - 1), N acting on the perturbation
+    steps of stack 2.  Exact rational evaluation with the hand-written pi N of m = 4
+    and small integer dynamic spectra."""
+    m = 4
+    d1 = np.array([[1, 0, 2], [0, -1, 1], [3, 1, 0], [-2, 2, -1]], dtype=np.float64)
+    d2 = np.array([[2, -1], [1, 0], [0, 3], [-1, 1]], dtype=np.float64)
+    piN = _PI_TIMES_N[m]
+    want_psi = [[sum(_F(int(d1[j, a])) * piN[j][k] * _F(int(d2[k, b]))
+                     for j in range(m) for k in range(m)) for b in range(2)] for a in range(3)]
+    want_phi = [[sum(_F(int(d1[j, a])) * _F(int(d2[j, b])) for j in range(m))
+                 for b in range(2)] for a in range(3)]
+    phi, psi = oracle.hilbert_noda(d1, d2)
+    assert np.allclose((m - 1) * phi, np.array(want_phi, dtype=np.float64), rtol=0, atol=1e-14)
+    assert np.allclose(math.pi * (m - 1) * psi, np.array(want_psi, dtype=np.float64), rtol=0,
+                       atol=1e-13)
+    # stack 2 swapped in: N then acts on the other stack, i.e. the transposed pairing
+    _, psi21 = oracle.hilbert_noda(d2, d1)
+    assert np.allclose(psi21, -psi.T, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("w", [0.3, 0.7, 1.5, 2.5])
+def test_hilbert_noda_of_a_sinusoid_is_the_cosine_times_the_kernel_gain(w):
+    """Eq. HT: with the paper's (1/pi) PV int y(t')/(t' - t) dt', the Hilbert transform
+    of sin(w t) is cos(w t).  The discrete kernel of Eq. HilbNoda, summed over the lags
+    l = k - j on both sides of a step, gives
+      z(t_j) = (2/pi) cos(w j + p) sum_{l=1}^{L} sin(w l)/l
+    for y = sin(w k + p), and the sawtooth Fourier series sum_{l>=1} sin(w l)/l =
+    (pi - w)/2 (0 < w < 2 pi) leaves z = (1 - w/pi) cos(w j + p) up to the series tail
+    beyond the window, |tail| <= 1/((L + 1) sin(w/2)).  An impulse d1 at the centre
+    step j0 reads z(t_j0) out of Psi."""
+    m, j0 = 2001, 1000
+    L = min(j0, m - 1 - j0)
+    k = np.arange(m)
+    d2 = np.stack([np.sin(w * k + 0.3), np.cos(w * k - 1.1)], axis=1)  # cos = sin(. + pi/2)
+    d1 = np.zeros((m, 1))
+    d1[j0, 0] = 1.0
+    _, psi = oracle.hilbert_noda(d1, d2)
+    z = (m - 1) * psi[0]
+    want = (1.0 - w / math.pi) * np.array([np.cos(w * j0 + 0.3), -np.sin(w * j0 - 1.1)])
+    bound = (2.0 / math.pi) / ((L + 1) * math.sin(w / 2.0))
+    assert np.max(np.abs(z - want)) <= bound
+
+
+@pytest.mark.parametrize("m,f", [(513, 20), (1025, 40)])
+def test_ft_and_ht_async_spectra_agree_on_a_single_tone(m, f):
+    """Sec. 2: the FT and HT approaches give the same spectra.  For bands varying as
+    sin(2 pi f j/m + phase) (f whole periods in the window) the FT's Psi is the closed
+    form Norm (m^2/2) a b sin(phase difference) and, far from the window edges, the HT's
+    is (m/2) a b (1 - w/pi) sin(...) / (m - 1) with w = 2 pi f/m (the previous pin): so
+    Psi_FT / Psi_HT = (m/pi) / (1 - w/pi) up to the edges' share, ~1/(m w) (below 1 %
+    here), while Phi_FT / Phi_HT = m/pi exactly (odd m)."""
+    t = np.arange(m)
+    nu = np.arange(40.0)
+    L1 = 1.0 / (1.0 + ((nu - 10.0) / 4.0) ** 2)
+    L2 = 1.0 / (1.0 + ((nu - 30.0) / 4.0) ** 2)
+    y = (np.outer(np.sin(2 * np.pi * f * t / m), L1) +
+         np.outer(np.sin(2 * np.pi * f * t / m + np.deg2rad(50.0)), L2)).astype(np.float32)
+    phi, psi, _, _ = oracle.corr2d(y)
+    d = oracle.dynamic(y, oracle.reference_mean(y))
+    hphi, hpsi = oracle.hilbert_noda(d, d)
+    w = 2 * np.pi * f / m
+    gain = (m / math.pi) / (1.0 - w / math.pi)
+    assert abs(psi[30, 10] / hpsi[30, 10] / gain - 1.0) < 0.02
+    assert psi[30, 10] > 0 and hpsi[30, 10] > 0  # band 2 leads band 1 (rule 3)
+    assert abs(phi[30, 10] / hphi[30, 10] / (m / math.pi) - 1.0) < 1e-12
+
+
 # ------------------------------------------------------------ interpolation
 
 def test_interp_matches_numpy_interp_and_endpoints():
@@ -417,6 +539,25 @@ def test_interp_reproduces_linear_functions_and_subtracts_reference():
     ref = np.linspace(0, 1, 37).astype(np.float32)
     out2, dyn = oracle.interp_linear(x, y, 37, ref=ref)
     assert np.array_equal(dyn, out2 - ref.astype(np.float64))
+
+
+def test_interp_dyn_out_is_the_dynamic_spectrum_of_the_correlation():
+    """Eq. dynspec after the spectral-axis preprocessing: correlating dyn_out as the
+    stack (user reference 0) equals correlating y_out against the reference itself;
+    the reference subtraction inside oracle.corr2d is pinned by the brute force of a
+    second formula (test_brute_force_user_reference_and_norm).  dyn_out of the
+    reference row itself is zero."""
+    rng = np.random.default_rng(8)
+    x = workloads.jittered_axis(90, 0.0, 40.0, rng)
+    y = workloads.random_stack(7, 90, seed=9, offset=1.5)
+    out0, _ = oracle.interp_linear(x, y, 64)
+    ref = out0[2].astype(np.float32)
+    out, dyn = oracle.interp_linear(x, y, 64, ref=ref)
+    zero = np.zeros(64, np.float32)
+    pa, qa, _, _ = oracle.corr2d(dyn.astype(np.float32), ref1=zero)
+    pb, qb, _, _ = oracle.corr2d(out.astype(np.float32), ref1=ref)
+    assert _rel(pa, pb) < 1e-6 and np.abs(qa - qb).max() < 1e-6 * np.abs(pb).max()
+    assert np.abs(dyn[2]).max() <= 1e-6 * np.abs(out[2]).max()
 
 
 def test_perturbation_interp_matches_numpy_per_variable():
