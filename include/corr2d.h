@@ -337,16 +337,30 @@ corr2d_status corr2d_get_kernel_info(corr2d_ctx* ctx, int* last_xspec, int* pair
  * library routine.
  *
  * - Precisions: CORR2D_PREC_SPLIT and CORR2D_PREC_BF16 (FP32: EUNSUPPORTED).
- * - Size limit: a problem needs about (n1 + n2) * rowbytes + twiddles, with
- *   rowbytes = 1 KB for m <= 257 in SPLIT (2 KB for m <= 513); anything larger
- *   than the array returns EUNSUPPORTED with the byte counts in `msg`, before
- *   any work is enqueued.  Example: homo n = 8000 at m = 256 fits.
- * - The first call on a device does a one-time set-up there (it looks up the
- *   array's device address with cudaGetSymbolAddress and sets kernel
- *   attributes); make that first call before any stream capture begins.
+ * - Flags: CORR2D_FLAG_HILBERT selects the Hilbert-transform approach as in
+ *   corr2d_compute (m <= 256, default norm 1/(m - 1)); CORR2D_FLAG_UPPER_TRIANGLE
+ *   stores only the upper triangle of a homo problem as in corr2d_compute;
+ *   CORR2D_FLAG_NO_MIRROR computes every tile.  Without NO_MIRROR a homo
+ *   problem always runs on mirrored tiles (no tuner here), so its Phi is
+ *   exactly symmetric and Psi exactly antisymmetric with a zero diagonal --
+ *   what CORR2D_FLAG_EXACT_SYMMETRY asks of corr2d_compute.
+ * - Size limit: a problem needs about rows * rowbytes + twiddles, with rows =
+ *   n1 for a homo problem (its two operands share one row set; the Hilbert
+ *   variant keeps two: 2 n1) and n1 + n2 for a hetero one, rowbytes = 1 KB for
+ *   m <= 257 in SPLIT (2 KB for m <= 513; the Hilbert variant: 2 m bytes
+ *   rounded up to 128); anything larger than the array returns EUNSUPPORTED
+ *   with the byte counts in `msg`, before any work is enqueued.  Example: homo
+ *   n = 30000 at m = 256 in SPLIT fits, homo n = 40000 does not.
+ * - The first call on a device does a one-time set-up there: it looks up the
+ *   array's device address with cudaGetSymbolAddress, which also loads the
+ *   library module that holds the array, so the array's device memory is
+ *   committed on that device by this first call (and kept until the process
+ *   exits), and it sets kernel attributes.  Make that first call at start-up:
+ *   before a memory planner claims the device, and before any stream capture
+ *   begins.
  * - The call is synchronous: it returns after the results are in phi/psi
  *   (it waits for `cuda_stream`) and reports CORR2D_ETIMEOUT if a device-side
- *   wait ran out.
+ *   wait ran out (limit 2 s, or CORR2D_WAIT_LIMIT_MS milliseconds).
  * - All calls share the one array and it keeps the last call's contents.
  *   Calls that overlap on the GPU (from several host threads or streams) race
  *   on it; serialise them.
@@ -357,6 +371,15 @@ corr2d_status corr2d_compute_noalloc(int device, void* cuda_stream, int m, int n
                                      const float* y1, int ld1, int n2, const float* y2, int ld2,
                                      const corr2d_params* params, float* phi, float* psi,
                                      long ldo, char* msg, size_t msg_len);
+
+/* Measured FP32 FMA throughput of the context's device in TFLOP/s (the
+ * paper has no counterpart: it is the ceiling against which the CUDA-core
+ * FP32 path, CORR2D_PREC_FP32, is reported).  A probe kernel of independent
+ * FMA chains (4 CTAs of 256 threads per SM) runs four times on the context's
+ * stream, the first as a warm-up; *tflops receives the best of the other three
+ * (2 flop per FMA).  Synchronous; allocates and frees a small device buffer.
+ * EINVAL for a NULL argument, ECUDA if the launch fails. */
+corr2d_status corr2d_measure_fp32_peak(corr2d_ctx* ctx, double* tflops);
 
 /* Library version string. */
 const char* corr2d_version(void);

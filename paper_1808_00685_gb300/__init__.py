@@ -43,7 +43,7 @@ EXPORTED_SYMBOLS = (
     "corr2d_compute_host", "corr2d_batch", "corr2d_version", "corr2d_set_profiling",
     "corr2d_get_timings", "corr2d_compute_noalloc", "corr2d_preprocess_perturbation",
     "corr2d_compute_rows", "corr2d_compute_reduced", "corr2d_interpolate_perturbation",
-    "corr2d_get_kernel_info",
+    "corr2d_get_kernel_info", "corr2d_measure_fp32_peak",
 )
 XSPEC_NONE, XSPEC_TC, XSPEC_TC_PAIR, XSPEC_FP32, XSPEC_TC_TA = range(5)
 
@@ -110,6 +110,7 @@ def load(path: str | None = None):
             "corr2d_get_timings": (i, [vp, ctypes.POINTER(ctypes.c_float),
                                        ctypes.POINTER(ctypes.c_float)]),
             "corr2d_get_kernel_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i)]),
+            "corr2d_measure_fp32_peak": (i, [vp, ctypes.POINTER(d)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -239,6 +240,13 @@ def corr2d_get_timings(ctx: int):
     return a.value, b.value
 
 
+def corr2d_measure_fp32_peak(ctx: int) -> float:
+    """Measured FP32 FMA throughput of the context's device, TFLOP/s."""
+    t = ctypes.c_double()
+    _check(ctx, load().corr2d_measure_fp32_peak(ctx, ctypes.byref(t)))
+    return t.value
+
+
 class BatchPlan:
     """corr2d_batch arguments for one list of problems (torch tensors), built
     once.  The tensors must stay alive while the plan is run."""
@@ -330,6 +338,10 @@ class Context:
     def timings(self):
         """(prep_ms, xspec_ms) of the last call (profiling must be on)."""
         return corr2d_get_timings(self.handle)
+
+    def fp32_peak_tflops(self) -> float:
+        """Measured FP32 FMA throughput of this device (TFLOP/s)."""
+        return corr2d_measure_fp32_peak(self.handle)
 
     def kernel_info(self):
         """(last cross-spectrum kernel: XSPEC_*, co-resident CTA pairs)."""

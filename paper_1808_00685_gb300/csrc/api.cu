@@ -807,6 +807,38 @@ corr2d_status corr2d_get_kernel_info(corr2d_ctx* ctx, int* last_xspec, int* pair
   return CORR2D_OK;
 }
 
+corr2d_status corr2d_measure_fp32_peak(corr2d_ctx* ctx, double* tflops) {
+  if (!ctx || !tflops) return CORR2D_EINVAL;
+  DeviceGuard g(ctx->device);
+  // 4 CTAs of 256 threads per SM: 32 warps, 8 independent chains each
+  const int blocks = 4 * ctx->sm_count, iters = 1 << 16;
+  DevBuf out;
+  corr2d_status st = ensure(ctx, out, (size_t)blocks * 256 * 4);
+  if (st != CORR2D_OK) return st;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(ctx, cudaEventCreate(&e0));
+  CUDA_TRY(ctx, cudaEventCreate(&e1));
+  float best = 1e30f;
+  cudaError_t e = cudaSuccess;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // a warm-up, then the best of 3
+    cudaEventRecord(e0, ctx->stream);
+    e = launch_fma_probe((float*)out.p, blocks, iters, ctx->stream);
+    cudaEventRecord(e1, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && e == cudaSuccess) best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  release(out);
+  if (e != cudaSuccess)
+    return fail(ctx, CORR2D_ECUDA, "FP32 probe failed: %s", cudaGetErrorString(e));
+  *tflops = fma_probe_flops(blocks, iters) / ((double)best * 1e-3) / 1e12;
+  ctx->err.clear();
+  return CORR2D_OK;
+}
+
 const char* corr2d_last_error(const corr2d_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_create_error.c_str();
 }

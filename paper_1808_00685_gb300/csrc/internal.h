@@ -176,6 +176,12 @@ cudaError_t launch_xspec_simt(int kp1, int n1, int n2, int ldp1, int ldp2, const
                               const float* s1, const float* s2, float norm, float* phi,
                               float* psi, long ldo, bool mirror, cudaStream_t s);
 
+// FP32 FMA throughput probe (measured ceiling of the FP32 path): `blocks` CTAs
+// of 256 threads, `iters` iterations of independent FMA chains; the flops one
+// launch performs.  `out` (blocks x 256 floats) is never written in practice.
+cudaError_t launch_fma_probe(float* out, int blocks, int iters, cudaStream_t s);
+double fma_probe_flops(int blocks, int iters);
+
 // Preprocessing.
 cudaError_t launch_interp(int m, int n_raw, const double* x, const float* y, int n_out,
                           float* out, const float* ref, float* dyn, int* err, cudaStream_t s);

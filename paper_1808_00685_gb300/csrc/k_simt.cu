@@ -235,4 +235,37 @@ cudaError_t launch_xspec_simt(int kp1, int n1, int n2, int ldp1, int ldp2, const
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// FP32 FMA throughput probe: the measured ceiling of the CUDA-core path.
+// Every thread runs FMA_CHAINS independent chains x <- x * a + b (latency
+// hidden by the chains and by 32 warps per SM), so the kernel is bound by the
+// FP32 pipe alone; 2 flop per FMA.  The result is stored only under a
+// condition the host makes false, so no chain can be removed.
+// ---------------------------------------------------------------------------
+constexpr int FMA_CHAINS = 8;
+
+__global__ void __launch_bounds__(256) k_fma_probe(float* out, int iters, float a, float b,
+                                                   float never) {
+  float x[FMA_CHAINS];
+#pragma unroll
+  for (int k = 0; k < FMA_CHAINS; ++k) x[k] = (float)(threadIdx.x + k) * 1e-3f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < FMA_CHAINS; ++k) x[k] = fmaf(x[k], a, b);
+  }
+  float acc = 0.f;
+#pragma unroll
+  for (int k = 0; k < FMA_CHAINS; ++k) acc += x[k];
+  if (acc == never) out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+cudaError_t launch_fma_probe(float* out, int blocks, int iters, cudaStream_t s) {
+  k_fma_probe<<<blocks, 256, 0, s>>>(out, iters, 0.999f, 1e-4f, -1.0f);
+  return cudaGetLastError();
+}
+
+double fma_probe_flops(int blocks, int iters) {
+  return 2.0 * FMA_CHAINS * (double)iters * (double)blocks * 256.0;
+}
+
 }  // namespace c2d

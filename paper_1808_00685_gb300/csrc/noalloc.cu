@@ -7,16 +7,24 @@
 // real-time loop that cannot afford the implicit device synchronisation of
 // cudaMalloc/cudaFree, or a caller that has no library context (creating one
 // allocates).  The caller still provides the stacks and the Phi/Psi outputs;
-// every intermediate (operand rows, scale vectors, twiddles, descriptors,
-// error word) lives in one fixed array of device memory that the library
-// declares at file scope.  The array is reserved on each GPU when the library
-// is loaded there and stays reserved until the process exits.
+// every intermediate (operand rows, scale vectors, contraction tables,
+// descriptors, error word) lives in one fixed array of device memory that the
+// library declares at file scope.
+//
+// When the array is committed: the library is built without relocatable
+// device code, so this file is a module of its own that holds only the array,
+// and CUDA loads modules lazily.  The array's memory is therefore committed on
+// a device by the first call there (its cudaGetSymbolAddress loads the
+// module), not when the library is loaded, and stays committed until the
+// process exits.  A caller whose memory planner will own the device should
+// make that first call at start-up, before the planner claims the memory.
 //
 // The kernels are the ones corr2d_compute uses (k_prep_tc, k_xspec_tc); only
 // where their scratch lives differs.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -175,22 +183,35 @@ extern "C" corr2d_status corr2d_compute_noalloc(int device, void* cuda_stream, i
     return say(msg, msg_len, CORR2D_EINVAL, "device %d is not available", device);
   }
 
+  const bool hilbert = (p.flags & CORR2D_FLAG_HILBERT) != 0;
+  if (hilbert && m > MAX_M_HT)
+    return say(msg, msg_len, CORR2D_EUNSUPPORTED,
+               "the Hilbert-transform variant supports m <= %d", MAX_M_HT);
+
   // ---- scratch plan: everything must fit the static array
+  // Operand rows: stack 1 and stack 2; a homo FT problem uses one row set for
+  // both operands (each row carries the square root of the half-spectrum
+  // weight), the Hilbert variant's two operands come from different matrices
+  // ([I; 0] and [I; -N]) and keep two.
   const int planes = p.precision == CORR2D_PREC_SPLIT ? 2 : 1;
-  const int kp = freq_padded(m, planes), nch = chunks_for(m, planes);
+  const int kp = comps_padded(m, planes, hilbert);
+  const int nch = kp / freq_group(planes);
   const int rowlen = nch * CHUNK_ELEMS;
-  const size_t tw_bytes = make_twiddles(m, planes, nullptr);
+  const bool shared_rows = homo && !hilbert;
+  const size_t tw_bytes = make_transform(m, planes, hilbert ? XF_HT_A : XF_DFT, nullptr);
+  const size_t tw2_bytes = hilbert ? make_transform(m, planes, XF_HT_B, nullptr) : 0;
   const int nt1 = (n1 + TILE_M - 1) / TILE_M, nt2 = (n2 + TILE_N - 1) / TILE_N;
   const bool mirror = homo && !(p.flags & CORR2D_FLAG_NO_MIRROR);
   const long nitems = mirror ? (long)nt1 * (nt1 + 1) / 2 : (long)nt1 * nt2;
-  const int njobs = homo ? 1 : 2;
-  const int npitems = nt1 + (homo ? 0 : (n2 + PREP_ROWS - 1) / PREP_ROWS);
+  const int njobs = shared_rows ? 1 : 2;
+  const int npitems = nt1 + (shared_rows ? 0 : (n2 + PREP_ROWS - 1) / PREP_ROWS);
   size_t off = 256;  // error word
   const size_t off_tw = off; off = up(off + tw_bytes, 1024);
+  const size_t off_tw2 = off; off = up(off + tw2_bytes, 1024);
   const size_t off_a = off;  off = up(off + (size_t)n1 * rowlen * 2, 1024);
-  const size_t off_b = off;  off = up(off + (size_t)n2 * rowlen * 2, 1024);
+  const size_t off_b = off;  off = up(off + (shared_rows ? 0 : (size_t)n2 * rowlen * 2), 1024);
   const size_t off_s1 = off; off = up(off + (size_t)n1 * 4, 256);
-  const size_t off_s2 = off; off = up(off + (size_t)n2 * 4, 256);
+  const size_t off_s2 = off; off = up(off + (homo ? 0 : (size_t)n2 * 4), 256);
   const size_t off_jobs = off; off = up(off + njobs * sizeof(PrepJob), 128);
   const size_t off_pit = off; off = up(off + npitems * sizeof(PrepItem), 128);
   const size_t off_prob = off; off = up(off + sizeof(XProblem), 128);
@@ -214,32 +235,39 @@ extern "C" corr2d_status corr2d_compute_noalloc(int device, void* cuda_stream, i
   cudaStream_t stream = (cudaStream_t)cuda_stream;
 
   // ---- host-side descriptors
-  std::vector<uint8_t> tw(tw_bytes);
-  make_twiddles(m, planes, tw.data());
+  std::vector<uint8_t> tw(tw_bytes), tw2(tw2_bytes);
+  make_transform(m, planes, hilbert ? XF_HT_A : XF_DFT, tw.data());
+  if (hilbert) make_transform(m, planes, XF_HT_B, tw2.data());
   uint16_t* opA = (uint16_t*)(S + off_a);
-  uint16_t* opB = (uint16_t*)(S + off_b);
+  uint16_t* opB = shared_rows ? opA : (uint16_t*)(S + off_b);
   float* s1 = (float*)(S + off_s1);
   float* s2 = homo ? s1 : (float*)(S + off_s2);
+  const float* ref1 = p.ref_mode == CORR2D_REF_USER ? p.ref1 : nullptr;
+  const float* ref2 = p.ref_mode == CORR2D_REF_USER ? (homo ? p.ref1 : p.ref2) : nullptr;
   std::vector<PrepJob> jobs(njobs);
   std::vector<PrepItem> pit;
   for (int jn = 0; jn < njobs; ++jn) {
+    // job 0: stack 1 -> opA (and opB when the rows are shared); job 1: the
+    // stack-2 operand (stack 1 again for a homo Hilbert problem) -> opB
     PrepJob& j = jobs[jn];
     memset(&j, 0, sizeof j);
     const bool second = jn == 1;
-    j.y = second ? y2 : y1;
-    j.ld = second ? ld2 : ld1;
-    j.n = second ? n2 : n1;
-    j.ref = p.ref_mode == CORR2D_REF_USER ? (second ? p.ref2 : p.ref1) : nullptr;
+    const bool from_y2 = second && !homo;
+    j.y = from_y2 ? y2 : y1;
+    j.ld = from_y2 ? ld2 : ld1;
+    j.n = from_y2 ? n2 : n1;
+    j.ref = from_y2 ? ref2 : ref1;
     j.outA = second ? nullptr : opA;
-    j.outB = (homo || second) ? opB : nullptr;
-    j.scale = second ? s2 : s1;
+    j.outB = second ? opB : nullptr;  // job 0 with shared rows: opB == opA
+    j.scale = from_y2 ? s2 : s1;      // a homo Hilbert problem writes s1 twice, same values
     j.sigma_out = nullptr;
-    j.wtab = S + off_tw;
+    j.wtab = S + ((second && hilbert) ? off_tw2 : off_tw);
     j.m = m;
     j.kp = kp;
     j.jchunks = (m + 63) / 64;
     j.rowlen = rowlen;
     j.alpha = p.alpha;
+    j.plain_weights = hilbert ? 1 : 0;
     for (int t = 0; t < (j.n + PREP_ROWS - 1) / PREP_ROWS; ++t) pit.push_back(PrepItem{jn, t});
   }
   XProblem xp;
@@ -253,13 +281,18 @@ extern "C" corr2d_status corr2d_compute_noalloc(int device, void* cuda_stream, i
     return say(msg, msg_len, CORR2D_ECUDA, "tensor map encoding failed");
   xp.s1 = s1;
   xp.s2 = s2;
-  xp.norm = (float)(p.norm > 0.0 ? p.norm : 1.0 / (kPi * (double)(m - 1)));
+  // Norm: the caller's, else 1/(pi (m-1)) (Eq. disint2d) or, for the Hilbert
+  // approach, 1/(m-1) (Eqs. disHTsyn, disHTasyn)
+  xp.norm = (float)(p.norm > 0.0 ? p.norm
+                                 : hilbert ? 1.0 / (double)(m - 1)
+                                           : 1.0 / (kPi * (double)(m - 1)));
   xp.n1 = n1;
   xp.n2 = n2;
   xp.nchunks = nch;
   xp.mirror = mirror ? 1 : 0;
   xp.bn = TILE_N;
   xp.out_row_tile0 = 0;
+  xp.upper_only = (mirror && (p.flags & CORR2D_FLAG_UPPER_TRIANGLE)) ? 1 : 0;
   std::vector<XItem> items;
   items.reserve(nitems);
   for (int ti = 0; ti < nt1; ++ti)
@@ -268,12 +301,19 @@ extern "C" corr2d_status corr2d_compute_noalloc(int device, void* cuda_stream, i
   // ---- enqueue: the error word starts at zero; the rest is written before it is read
   cudaError_t e = cudaMemsetAsync(S, 0, 256, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S + off_tw, tw.data(), tw_bytes, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess && hilbert)
+    e = cudaMemcpyAsync(S + off_tw2, tw2.data(), tw2_bytes, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S + off_jobs, jobs.data(), njobs * sizeof(PrepJob), cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S + off_pit, pit.data(), pit.size() * sizeof(PrepItem), cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S + off_prob, &xp, sizeof xp, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S + off_xit, items.data(), items.size() * sizeof(XItem), cudaMemcpyHostToDevice, stream);
   int* err = (int*)S;
-  const unsigned long long limit_ns = 2000000000ull;
+  // bounded device-side waits: 2 s, or CORR2D_WAIT_LIMIT_MS as for contexts
+  unsigned long long limit_ns = 2000000000ull;
+  if (const char* lim = getenv("CORR2D_WAIT_LIMIT_MS")) {
+    const long v = atol(lim);
+    if (v > 0) limit_ns = (unsigned long long)v * 1000000ull;
+  }
   if (e == cudaSuccess)
     e = launch_prep_tc((const PrepJob*)(S + off_jobs), (const PrepItem*)(S + off_pit),
                        (int)pit.size(), planes, kp, err, limit_ns, stream);

@@ -80,10 +80,15 @@ def run(ctx, y1, y2=None, kind="ta", tiles=None, expect=None, **kw):
 
 
 def check(phi, psi, ophi, opsi, tol, what):
+    """Relative Frobenius error within tol, and every element within 4 x tol x the
+    largest oracle magnitude of the pair (as in test_gpu_parity.check)."""
     ep, eq = rel(phi, ophi), rel(psi, opsi)
     mp, mq = np.abs(phi - ophi).max(), np.abs(psi - opsi).max()
-    assert ep <= tol and eq <= tol, (f"{what}: rel Phi {ep:.3e} Psi {eq:.3e}; "
-                                     f"max-abs Phi {mp:.3e} Psi {mq:.3e}")
+    big = max(np.abs(ophi).max(), np.abs(opsi).max())
+    msg = (f"{what}: rel Phi {ep:.3e} Psi {eq:.3e}; max-abs Phi {mp:.3e} Psi {mq:.3e} "
+           f"(largest magnitude {big:.3e})")
+    assert ep <= tol and eq <= tol, msg
+    assert mp <= 4.0 * tol * big and mq <= 4.0 * tol * big, msg
 
 
 @pytest.mark.parametrize("m,n", [(11, 100), (64, 64), (33, 200), (64, 300), (200, 384),
