@@ -3,9 +3,17 @@
 
 Default workload: homo correlation, m = 256 perturbation steps, n = 32768
 spectral variables, FP16 hi/lo split precision (32768^2 complex outputs,
-8.6 GB of Phi and Psi per step).  A step is one corr2d_compute call: FP64
-reference/centering/sigma + tcgen05 DFT kernel, then the tcgen05
+8.6 GB of Phi and Psi per step).  A step is one corr2d_compute call: the
+tcgen05 DFT kernel (reference, centering, sigma, transform), then the tcgen05
 cross-spectrum kernel.  Prints one JSON line (rank 0).
+
+The default run also times the comparison forms the metric names, on the same
+inputs, L2 flush and CUDA-event timing ("forms" in the JSON line): the plain
+FP32 GPU path and BF16 on the same problem, the upper-triangle output, and the
+batched form (512 problems of uneven m, n1, n2) against one call per problem
+and against the FP32 path per problem.  Their errors against the FP64 oracle,
+on sampled outputs, come from the CPU-baseline leg, the one place the oracle
+runs.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload c4|c2|c3|c5] [--precision split|bf16|fp32]
@@ -26,6 +34,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -34,6 +43,7 @@ sys.path.insert(0, ROOT)
 METRIC = "2D-corr output elems/s & % HBM roofline, split-prec vs FP32 at 1e-5 rel err"
 UNIT = "output elems/s"
 L2_FLUSH_BYTES = 256 << 20
+TOL = {"split": 1e-5, "fp32": 1e-5, "bf16": 1e-2}
 
 
 def parse_args():
@@ -47,8 +57,16 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the comparison forms (FP32, BF16, upper triangle, batch)")
     ap.add_argument("--no-batch", action="store_true",
                     help="c5 only: one corr2d_compute call per problem instead of corr2d_batch")
+    ap.add_argument("--upper-triangle", action="store_true",
+                    help="homo workloads: store only the upper triangle (half the outputs)")
+    ap.add_argument("--l2", choices=["clean", "dirty"], default="clean",
+                    help="L2 flush before every step: write a 256 MB buffer, then (clean) read "
+                         "another so that the flush's dirty lines are written back before the "
+                         "step, or (dirty) leave them in L2")
     ap.add_argument("--n", type=int, default=0,
                     help="small profiling cases: c4 keeps the first N spectral variables, "
                          "c5 gives every stack N variables (same m mix)")
@@ -88,9 +106,23 @@ def workload(name, precision, n_override=0):
                 alpha=0.0), spec
 
 
+def l2_text(mode):
+    if mode == "clean":
+        return ("flushed before every timed step outside the step's events: a 256 MB write, "
+                "then a 256 MB read of another buffer, so that L2 holds no dirty lines of the "
+                "flush when the step starts; each step writes >= 134 MB of output")
+    return ("flushed before every timed step (256 MB write outside the step's events); each "
+            "step writes >= 134 MB of output")
+
+
+def config_for(desc, world, l2_mode, parallelism=None):
+    return {**desc, "l2": l2_text(l2_mode),
+            "parallelism": parallelism or f"weak: one independent problem per GPU x{world}"}
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi clocks/throttle sampling during the timed region."""
+    """nvidia-smi clocks/throttle sampling during the timed region (log in a temp file)."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -98,10 +130,10 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        fd, self.path = tempfile.mkstemp(prefix=f"corr2d_clocks_gpu{gpu_index}_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
@@ -113,6 +145,7 @@ class ClockSampler:
 
     def stop(self):
         if not self.proc:
+            self._remove()
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         time.sleep(0.2)
         self.proc.terminate()
@@ -136,8 +169,15 @@ class ClockSampler:
                 for nm, val in zip(names, parts[5:9]):
                     if val.lower().startswith("active"):
                         reasons.add(nm)
+        self._remove()
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+    def _remove(self):
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
 
 
 # ---------------------------------------------------------------- helpers
@@ -195,6 +235,53 @@ def rowlen_elems(m, precision):
     return kp // g * 64
 
 
+def gpu_numa_cpus(device_index):
+    """(NUMA node, CPU list) of the host node the GPU hangs off, from sysfs; (None, None)
+    where that is not known."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(device_index)
+        path = (f"/sys/bus/pci/devices/{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:"
+                f"{p.pci_device_id:02x}.0/numa_node")
+        node = int(open(path).read().strip())
+        if node < 0:
+            return None, None
+        text = open(f"/sys/devices/system/node/node{node}/cpulist").read().strip()
+        cpus = set()
+        for part in text.split(","):
+            a, _, b = part.partition("-")
+            cpus |= set(range(int(a), int(b or a) + 1))
+        cpus &= set(os.sched_getaffinity(0))
+        return node, (sorted(cpus) or None)
+    except (OSError, ValueError, AttributeError, RuntimeError):
+        return None, None
+
+
+def link_bandwidth(h, d, stream, reps=3):
+    """Best-of-reps pinned host<->device copy bandwidth (GB/s) of 1 GiB each way,
+    with the buffers the end-to-end run uses."""
+    import torch
+    nb = min(1 << 30, h.numel() * h.element_size(), d.numel() * d.element_size())
+    hb = h.view(-1).view(torch.uint8)[:nb]
+    db = d.view(-1).view(torch.uint8)[:nb]
+    res = {}
+    with torch.cuda.stream(stream):
+        for name, (dst, src) in (("h2d_gbs", (db, hb)), ("d2h_gbs", (hb, db))):
+            dst.copy_(src, non_blocking=True)
+            stream.synchronize()
+            best = 1e30
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                dst.copy_(src, non_blocking=True)
+                e1.record(stream)
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            res[name] = round(nb / (best / 1e3) / 1e9, 1)
+    return res
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -223,6 +310,94 @@ def reduce_max(pg, value, device):
 def barrier(pg):
     if pg is not None:
         pg.barrier()
+
+
+# ---------------------------------------------------------------- timing
+class Flusher:
+    """L2 flush between steps: write a 256 MB buffer; in the clean mode also read a
+    second one, so that the flush's dirty lines are written back before the step."""
+
+    def __init__(self, device, mode):
+        import torch
+        self.mode = mode
+        self.w = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+        self.r = (torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+                  if mode == "clean" else None)
+
+    def __call__(self):
+        self.w.zero_()
+        if self.r is not None:
+            self.r.max()
+
+
+def timed_steps(ctx, stream, step, flush, steps, warmup, per_call_timing=True):
+    """Warm-up steps exactly like the timed ones (flush, events, step, per-kernel
+    timings), then `steps` timed steps, each bracketed by CUDA events on the stream
+    the library launches on.  Returns per-step, prep and cross-spectrum times (ms)."""
+    import torch
+    ctx.set_profiling(per_call_timing)
+    for _ in range(max(warmup, 0)):
+        flush()
+        w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0.record(stream)
+        step()
+        w1.record(stream)
+        if per_call_timing:
+            ctx.timings()
+        w1.synchronize()
+    ctx.synchronize()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    prep_ms, xspec_ms = [], []
+    for k in range(steps):
+        flush()  # outside the step's events
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        if per_call_timing:
+            p_ms, x_ms = ctx.timings()  # waits for this step's kernel events
+            prep_ms.append(p_ms)
+            xspec_ms.append(x_ms)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    ctx.synchronize()  # raises on a device-side time-out
+    return dict(step_ms=[a.elapsed_time(b) for a, b in ev], prep_ms=prep_ms, xspec_ms=xspec_ms,
+                region_ms=r0.elapsed_time(r1))
+
+
+def sample_block(n, upper=False):
+    """Sampled rows x columns of an n x n map where the errors are taken (first and
+    last indices included).  For an upper-triangle output the rows come from the
+    first half and the columns from the second, so that every entry has nu2 > nu1."""
+    import workloads as wl
+    if not upper:
+        return wl.sample_rows(n, 256, seed=41), wl.sample_rows(n, 256, seed=42)
+    h = n // 2
+    return wl.sample_rows(h, 128, seed=43), h + wl.sample_rows(n - h, 128, seed=44)
+
+
+def gather(phi, psi, rows, cols):
+    """Phi/Psi at rows x cols, to host FP64 (numpy)."""
+    import numpy as np
+    import torch
+    rt = torch.from_numpy(np.asarray(rows, np.int64)).to(phi.device)
+    ct = torch.from_numpy(np.asarray(cols, np.int64)).to(phi.device)
+    return (phi.index_select(0, rt).index_select(1, ct).double().cpu().numpy(),
+            psi.index_select(0, rt).index_select(1, ct).double().cpu().numpy())
+
+
+def error_of(got, want):
+    """Relative Frobenius and max-abs errors of Phi and Psi against the oracle."""
+    import numpy as np
+    (gp, gq), (op, oq) = got, want
+    big = max(float(np.abs(op).max()), float(np.abs(oq).max()), 1e-300)
+    return {"rel_err_phi": float(np.linalg.norm(gp - op) / max(np.linalg.norm(op), 1e-300)),
+            "rel_err_psi": float(np.linalg.norm(gq - oq) / max(np.linalg.norm(oq), 1e-300)),
+            "max_abs_phi": float(np.abs(gp - op).max()), "max_abs_psi": float(np.abs(gq - oq).max()),
+            "largest_magnitude": big}
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -254,21 +429,163 @@ def cpu_oracle_rate(y, n_sample=0, alpha=0.0, target_s=15.0):
                f"({n_sample * n_sample} outputs, {dt:.1f} s)", seconds=dt)
 
 
+def oracle_at(y1, y2, rows, cols, alpha=0.0):
+    """The oracle's Phi/Psi at rows x cols.  Reference, centering, sigma and DFT act on
+    one spectral variable at a time, so correlating the sampled columns of the stacks
+    gives exactly those entries (the oracle pin test_sampled_columns_give_those_entries)."""
+    import numpy as np
+    import oracle
+    ys2 = y1 if y2 is None else y2
+    phi, psi, _, _ = oracle.corr2d(np.ascontiguousarray(y1[:, rows]),
+                                   np.ascontiguousarray(ys2[:, cols]), alpha=alpha,
+                                   nthreads=oracle.max_threads())
+    return phi, psi
+
+
+def cpu_baseline_leg(args, y, alpha, checks):
+    """The one place the oracle runs: its timing on a bounded sample of the workload
+    (the CPU baseline) and its values at the sampled outputs of every timed form
+    (checks: name -> (y1, y2, rows, cols, alpha, gpu values)), from which the forms'
+    errors are computed.  Returns (cpu_baseline dict or None, errors by form)."""
+    cpu = None
+    if y is not None and not args.no_cpu_baseline:
+        rate, info = cpu_oracle_rate(y, args.cpu_sample_n, alpha)
+        cpu = {"value": rate, "unit": UNIT, **{k: v for k, v in info.items() if k != "seconds"}}
+    errors = {}
+    t0 = time.perf_counter()
+    for name, entries in checks.items():
+        worst = None
+        for (y1, y2, rows, cols, a, got) in entries:
+            e = error_of(got, oracle_at(y1, y2, rows, cols, a))
+            if worst is None:
+                worst = e
+            else:  # worst problem of a batch, by relative error
+                for k in e:
+                    worst[k] = max(worst[k], e[k])
+        if worst is not None:
+            worst["sampled"] = (f"{len(entries)} problem(s), "
+                                f"{sum(len(r) * len(c) for (_, _, r, c, _, _) in entries)} outputs")
+            errors[name] = worst
+    if cpu is not None and checks:
+        cpu["checks_s"] = round(time.perf_counter() - t0, 2)
+    return cpu, errors
+
+
+# ---------------------------------------------------------------- forms
+def run_forms(args, ctx, stream, flush, y, yd, phi, psi, ldo, rows, cols, checks):
+    """Comparison forms of the metric on the same inputs, flush and timing: c4 in FP32,
+    BF16 and upper-triangle output; the batch of 512 problems batched, per problem
+    and per problem in FP32.  Sampled GPU outputs go into `checks`."""
+    import torch
+    import paper_1808_00685_gb300 as pkg
+    import workloads as wl
+    forms = {}
+    m, n = y.shape
+    peak_fp32 = ctx.fp32_peak_tflops()
+    peak, _ = measured_peaks()
+
+    def c4_form(name, **kw):
+        def step():
+            ctx.compute(yd, out=(phi, psi), **kw)
+        t = timed_steps(ctx, stream, step, flush, args.steps, args.warmup)
+        ms = statistics.mean(t["step_ms"])
+        xms = statistics.mean(t["xspec_ms"])
+        upper = kw.get("upper_triangle", False)
+        outs = n * (n + 1) / 2 if upper else n * n
+        d = {"workload": f"homo m={m} n={n} {kw.get('precision', 'split')}"
+                         + (" upper triangle" if upper else ""),
+             "ms_per_step": round(ms, 4), "value": n * n / (ms / 1e3),
+             "kernel_ms": round(xms, 4), "prep_ms": round(statistics.mean(t["prep_ms"]), 4),
+             "steps": args.steps}
+        prec = kw.get("precision", "split")
+        if prec == "fp32":
+            kp1 = (m - 1) // 2 + 1
+            ach = 8.0 * kp1 * (n * (n + 1) / 2) / (xms / 1e3) / 1e12  # unique pairs of a homo map
+            d["roofline"] = {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak_fp32, 1),
+                             "unit": "TFLOP/s", "frac": round(ach / peak_fp32, 4),
+                             "peak_kind": "measured: FP32 FMA probe kernel (corr2d_measure_fp32_peak)"}
+        else:
+            xb = 8.0 * outs + 1.0 * n * rowlen_elems(m, prec) * 2
+            ach = xb / (xms / 1e3) / 1e9
+            d["roofline"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+                             "unit": "GB/s", "frac": round(ach / peak, 4),
+                             "algorithmic_bytes_per_launch": xb}
+        r, c = sample_block(n, upper)
+        checks[name] = [(y, None, r, c, 0.0, gather(phi, psi, r, c))]
+        return d
+
+    forms["fp32"] = c4_form("fp32", precision="fp32")
+    forms["bf16"] = c4_form("bf16", precision="bf16")
+    forms["upper_triangle"] = c4_form("upper_triangle", precision="split", upper_triangle=True)
+
+    # the batched form: 512 problems, m ~ U{8..200}, n log-uniform [256, 8192]
+    spec = wl.c5_spec()
+    ins = wl.batch_inputs(spec)
+    probs = []
+    for (y1, y2), p in zip(ins, spec.problems):
+        d1 = torch.from_numpy(y1).to(yd.device)
+        d2 = None if y2 is None else torch.from_numpy(y2).to(yd.device)
+        ph, ps, _ = pkg.Context.alloc_out(p.n1, p.n2, yd.device)
+        probs.append((d1, d2, ph, ps))
+    outputs = spec.total_outputs
+    samp = [(wl.sample_rows(p.n1, 4, seed=9000 + i), wl.sample_rows(p.n2, 48, seed=19000 + i))
+            for i, p in enumerate(spec.problems)]
+
+    def c5_checks():
+        out = []
+        for (y1, y2), (_, _, ph, ps), (r, c) in zip(ins, probs, samp):
+            out.append((y1, y2, r, c, 0.0, gather(ph, ps, r, c)))
+        return out
+
+    def c5_form(name, step, per_call):
+        t = timed_steps(ctx, stream, step, flush, args.steps, args.warmup, per_call)
+        ms = statistics.mean(t["step_ms"])
+        d = {"workload": f"batched {len(probs)} problems m~U[8,200] n log-uniform [256,8192] "
+                         + name, "ms_per_step": round(ms, 4), "value": outputs / (ms / 1e3),
+             "steps": args.steps}
+        if per_call:
+            xms = statistics.mean(t["xspec_ms"])
+            d["kernel_ms"] = round(xms, 4)
+            d["prep_ms"] = round(statistics.mean(t["prep_ms"]), 4)
+            ach = 8.0 * outputs / (xms / 1e3) / 1e9
+            d["roofline"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+                             "unit": "GB/s", "frac": round(ach / peak, 4),
+                             "algorithmic_bytes_per_launch": 8.0 * outputs}
+        checks[name] = c5_checks()
+        return d
+
+    plan = ctx.batch_plan(probs, precision="split")
+    forms["c5_batch"] = c5_form("c5_batch", plan.run, True)
+
+    def per_problem(prec):
+        def step():
+            for d1, d2, ph, ps in probs:
+                ctx.compute(d1, d2, precision=prec, out=(ph, ps))
+        return step
+    forms["c5_per_problem"] = c5_form("c5_per_problem", per_problem("split"), False)
+    forms["c5_fp32_per_problem"] = c5_form("c5_fp32_per_problem", per_problem("fp32"), False)
+    del probs, plan
+    torch.cuda.empty_cache()
+    return forms, peak_fp32
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args, world, rank, local, pg):
     import numpy as np
     import torch
 
     import paper_1808_00685_gb300 as pkg
+    import workloads as wl
 
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     stream = torch.cuda.current_stream(device)
     desc, inputs = workload(args.workload, args.precision, args.n)
     ctx = pkg.Context(local, stream)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    flush = Flusher(device, args.l2)
     launches_per_step = 2
     per_call_timing = True  # the step is one library call: its kernel events time it
+    upper = args.upper_triangle and args.workload in ("c4", "c2")
 
     if args.workload in ("c4", "c2"):
         y, _ = inputs
@@ -278,9 +595,14 @@ def run_ours(args, world, rank, local, pg):
         outputs = n * n
 
         def step():
-            ctx.compute(yd, precision=args.precision, out=(phi, psi))
-        # Phi and Psi stored, the homo problem's one operand row set read once
-        xbytes = 8.0 * n * n + 1.0 * n * rowlen_elems(m, args.precision) * 2
+            ctx.compute(yd, precision=args.precision, out=(phi, psi), upper_triangle=upper)
+        # Phi and Psi stored (the upper triangle only: n (n + 1) / 2 pairs), the homo
+        # problem's one operand row set read once
+        stored = n * (n + 1) / 2 if upper else n * n
+        xbytes = 8.0 * stored + 1.0 * n * rowlen_elems(m, args.precision) * 2
+        if upper:
+            desc["workload"] += " upper triangle"
+            desc["upper_triangle"] = True
     elif args.workload == "c3":
         raw = inputs
         x1, y1r = torch.from_numpy(raw.x1).to(device), torch.from_numpy(raw.y1).to(device)
@@ -298,7 +620,6 @@ def run_ours(args, world, rank, local, pg):
         y = raw.y1
     else:
         spec = inputs
-        import workloads as wl
         ins = wl.batch_inputs(spec)
         probs = []
         for (y1, y2), p in zip(ins, spec.problems):
@@ -330,84 +651,80 @@ def run_ours(args, world, rank, local, pg):
     sampler = ClockSampler(local)
     sampler.start()
     try:
-        ctx.set_profiling(True)
-        # warm-up steps run exactly like the timed ones (flush, events, step,
-        # per-kernel timings), so that no first-use cost lands in a timed step
-        for _ in range(max(args.warmup, 0)):
-            flush.zero_()
-            w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            w0.record(stream)
-            step()
-            w1.record(stream)
-            ctx.timings()
-            w1.synchronize()
-        ctx.synchronize()
-        torch.cuda.synchronize()
-        kind, pair_clusters = ctx.kernel_info()
-        kernel = {pkg.XSPEC_TC: "k_xspec_tc", pkg.XSPEC_TC_PAIR: "k_xspec_pair",
-                  pkg.XSPEC_TC_TA: "k_xspec_ta",
-                  pkg.XSPEC_FP32: "k_xspec_simt"}.get(kind, "none")
         barrier(pg)
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        r0.record(stream)
-        prep_ms, xspec_ms = [], []
-        for k in range(args.steps):
-            flush.zero_()  # L2 flush, outside the step's events
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-            p_ms, x_ms = ctx.timings()  # waits for this step's kernel events
-            prep_ms.append(p_ms)
-            xspec_ms.append(x_ms)
-        r1.record(stream)
-        torch.cuda.synchronize()
+        t = timed_steps(ctx, stream, step, flush, args.steps, args.warmup, per_call_timing)
         barrier(pg)
     except BaseException:
         sampler.stop()  # no nvidia-smi left running
         raise
     clocks = sampler.stop()
-    ctx.synchronize()  # raises on a device-side time-out
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = statistics.mean(step_ms)
+    kind, pair_clusters = ctx.kernel_info()
+    kernel = {pkg.XSPEC_TC: "k_xspec_tc", pkg.XSPEC_TC_PAIR: "k_xspec_pair",
+              pkg.XSPEC_TC_TA: "k_xspec_ta", pkg.XSPEC_FP32: "k_xspec_simt"}.get(kind, "none")
+    ms = statistics.mean(t["step_ms"])
     ms_max = reduce_max(pg, ms, device)
     value = world * outputs / (ms_max / 1e3)
 
     peak, peak_kind = measured_peaks()
     # several calls per step: the per-kernel events cover the last call only,
     # so the whole step time stands in for the kernel time
-    x_mean = statistics.mean(xspec_ms) if per_call_timing else ms
+    x_mean = statistics.mean(t["xspec_ms"]) if per_call_timing else ms
     achieved = xbytes / (x_mean / 1e3) / 1e9
     traffic = xspec_traffic_per_launch(args.workload, args.precision, kernel)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kernel,
                 "grid": (f"{pair_clusters} CTA pairs" if kernel == "k_xspec_pair" else None),
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": xbytes,
-                "kernel_ms": round(x_mean, 4), "prep_ms": round(statistics.mean(prep_ms), 4)}
+                "kernel_ms": round(x_mean, 4),
+                "prep_ms": round(statistics.mean(t["prep_ms"]), 4) if t["prep_ms"] else None}
     if args.precision != "fp32":
         # second denominator: the write-only stream (measured after the timed region)
         st = store_stream_gbs(device)
         roofline.update({"store_stream_gbs": st, "frac_of_store_stream": round(achieved / st, 4)})
     if args.precision == "fp32":
-        roofline["bound"] = "alu"
-        fp32_peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
+        fp32_peak = ctx.fp32_peak_tflops()
         kp1 = (desc.get("m", 2) - 1) // 2 + 1
         n_ = desc.get("n1", 0)
         # 8 flops per output and frequency, unique outputs of a homo problem
         flops = 8.0 * kp1 * (n_ * (n_ + 1) / 2 if desc.get("homo") else outputs)
         ach = flops / (x_mean / 1e3) / 1e12
-        roofline.update({"achieved": round(ach, 2), "peak": round(fp32_peak_tflops, 1),
-                         "unit": "TFLOP/s", "frac": round(ach / fp32_peak_tflops, 4),
-                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"})
+        roofline.update({"bound": "alu", "achieved": round(ach, 2), "peak": round(fp32_peak, 1),
+                         "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
+                         "peak_kind": "measured: FP32 FMA probe kernel (corr2d_measure_fp32_peak)"})
 
-    # end to end through the host-buffer entry point (pinned host memory)
+    # sampled outputs of the main run, for its error against the oracle
+    checks = {}
+    rows = cols = None
+    if args.workload in ("c4", "c2") and rank == 0:
+        rows, cols = sample_block(n, upper)
+        checks["main"] = [(y, None, rows, cols, 0.0, gather(phi, psi, rows, cols))]
+
+    forms = None
+    if (not args.no_forms and args.workload == "c4" and args.precision == "split" and not upper
+            and world == 1 and not args.n):
+        sampler2 = ClockSampler(local)
+        sampler2.start()
+        try:
+            forms, _ = run_forms(args, ctx, stream, flush, y, yd, phi, psi, ldo, rows, cols,
+                                 checks)
+        finally:
+            forms_clocks = sampler2.stop()
+        forms["clocks"] = forms_clocks
+
+    # end to end through the host-buffer entry point (pinned host memory placed on
+    # the GPU's NUMA node when sysfs names it)
     e2e = None
     if not args.no_e2e and args.workload in ("c4", "c2"):
-        y_h = torch.from_numpy(y).pin_memory()
-        phi_h = torch.empty((n, n), dtype=torch.float32).pin_memory()
-        psi_h = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        node, cpus = gpu_numa_cpus(local)
+        saved = os.sched_getaffinity(0)
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+        try:
+            y_h = torch.from_numpy(y).pin_memory()
+            phi_h = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
+            psi_h = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
+        finally:
+            os.sched_setaffinity(0, saved)
         ctx.compute_host(y_h, precision=args.precision, out=(phi_h, psi_h))  # warm-up
         times = []
         for _ in range(max(args.e2e_steps, 1)):
@@ -415,16 +732,38 @@ def run_ours(args, world, rank, local, pg):
             ctx.compute_host(y_h, precision=args.precision, out=(phi_h, psi_h))
             times.append(time.perf_counter() - t0)
         e2e_s = reduce_max(pg, statistics.mean(times), device)
+        link = link_bandwidth(phi_h, phi, stream)
+        h2d_b, d2h_b = int(y.nbytes), int(2 * n * n * 4)
+        link_ms = (h2d_b / (link["h2d_gbs"] * 1e9) + d2h_b / (link["d2h_gbs"] * 1e9)) * 1e3
         e2e = {"value": world * outputs / e2e_s, "unit": UNIT,
-               "h2d_bytes_per_step": int(y.nbytes), "d2h_bytes_per_step": int(2 * n * n * 4),
-               "api": "corr2d_compute_host", "ms_per_step": round(e2e_s * 1e3, 2)}
+               "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": d2h_b,
+               "api": "corr2d_compute_host", "ms_per_step": round(e2e_s * 1e3, 2),
+               "link": {**link, "numa_node": node,
+                        "pinned_on": "GPU's NUMA node" if cpus else "default placement",
+                        "copy_bound_ms": round(link_ms, 2),
+                        "frac_of_copy_bound": round(link_ms / (e2e_s * 1e3), 4)}}
         del phi_h, psi_h, y_h
 
     ctx.close()
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and y is not None:
-        rate, info = cpu_oracle_rate(y, args.cpu_sample_n, desc.get("alpha", 0.0))
-        cpu = {"value": rate, "unit": UNIT, **{k: v for k, v in info.items() if k != "seconds"}}
+    errors = {}
+    if rank == 0 and world == 1:
+        cpu, errors = cpu_baseline_leg(args, y, desc.get("alpha", 0.0), checks)
+    if forms is not None:
+        for name, e in errors.items():
+            if name in forms:
+                forms[name]["error"] = e
+                forms[name]["within_tol"] = bool(
+                    e["rel_err_phi"] <= TOL.get("bf16" if name == "bf16" else "split")
+                    and e["rel_err_psi"] <= TOL.get("bf16" if name == "bf16" else "split"))
+        x_ms = roofline["kernel_ms"]
+        forms["speedup"] = {
+            "split_vs_fp32_c4_step": round(forms["fp32"]["ms_per_step"] / ms_max, 2),
+            "split_vs_fp32_c4_kernel": round(forms["fp32"]["kernel_ms"] / x_ms, 2),
+            "batch_vs_per_problem_c5": round(forms["c5_per_problem"]["ms_per_step"] /
+                                             forms["c5_batch"]["ms_per_step"], 2),
+            "batch_vs_fp32_per_problem_c5": round(forms["c5_fp32_per_problem"]["ms_per_step"] /
+                                                  forms["c5_batch"]["ms_per_step"], 2)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -434,13 +773,15 @@ def run_ours(args, world, rank, local, pg):
                   "bf16": "bf16, f32 accumulate (double-float f32 centering)",
                   "fp32": "f32 (f64 centering)"}[args.precision],
         "data": "synthetic (seeded band spectra; the paper's datasets are not available)",
-        "config": {**desc, "l2": "flushed before every timed step (256 MB write outside the "
-                                 "step's events); each step writes >= 134 MB of output",
-                   "parallelism": f"weak: one independent problem per GPU x{world}"},
+        "config": config_for(desc, world, args.l2),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches_per_step * args.steps,
-        "region_ms": round(r0.elapsed_time(r1), 3),
+        "region_ms": round(t["region_ms"], 3),
     }
+    if "main" in errors:
+        line["error"] = errors["main"]
+    if forms is not None:
+        line["forms"] = forms
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -456,7 +797,6 @@ def run_reference(args, world, rank):
         y = inputs.y1
     else:
         y = inputs[0]
-    import oracle
     rates = []
     n_s = args.cpu_sample_n or 0
     info = None
@@ -473,7 +813,7 @@ def run_reference(args, world, rank):
         "warmup": args.warmup, "ms_per_step": round(statistics.mean(ms), 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded band spectra; the paper's datasets are not available)",
-        "config": desc, "impl": "reference",
+        "config": config_for(desc, world, args.l2), "impl": "reference",
         "cpu_baseline": {"value": value, "unit": UNIT, "kind": info["kind"],
                          "cores": info["cores"], "sample": info["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
