@@ -734,9 +734,9 @@ corr2d_status corr2d_create(corr2d_ctx** out, int device, void* cuda_stream) {
   for (int i = 0; i < 3; ++i)
     if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess)
       return fail(nullptr, CORR2D_ECUDA, "cannot create timing events");
-  if (cudaMalloc(&ctx->d_err, 256) != cudaSuccess)
+  if (cudaMalloc(&ctx->d_err, ERR_BLOCK_BYTES) != cudaSuccess)
     return fail(nullptr, CORR2D_ENOMEM, "cannot allocate the error word");
-  if (cudaMemset(ctx->d_err, 0, 256) != cudaSuccess)
+  if (cudaMemset(ctx->d_err, 0, ERR_BLOCK_BYTES) != cudaSuccess)
     return fail(nullptr, CORR2D_ECUDA, "cannot clear the error word");
   if (const char* lim = getenv("CORR2D_WAIT_LIMIT_MS")) {
     long v = atol(lim);
@@ -852,7 +852,8 @@ corr2d_status corr2d_synchronize(corr2d_ctx* ctx) {
   int word = 0;
   CUDA_TRY(ctx, cudaMemcpy(&word, ctx->d_err, sizeof word, cudaMemcpyDeviceToHost));
   if (word != DEV_OK) {
-    CUDA_TRY(ctx, cudaMemset(ctx->d_err, 0, sizeof word));
+    // the error word and the cross-spectrum kernel's work counters
+    CUDA_TRY(ctx, cudaMemset(ctx->d_err, 0, ERR_BLOCK_BYTES));
     if (word == DEV_BAD_AXIS)
       return fail(ctx, CORR2D_EINVAL, "preprocess: raw axis is not strictly increasing and finite");
     return fail(ctx, CORR2D_ETIMEOUT, "a device-side wait exceeded its limit; results are invalid");

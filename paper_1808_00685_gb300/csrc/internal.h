@@ -195,4 +195,12 @@ cudaError_t launch_spline_t(int m, int n, const double* t, const float* y, long 
 // preprocessing axis check failed.
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD_AXIS = 2 };
 
+// The error word `err` every launcher takes is the first int of a 256-byte,
+// zero-initialised block; ints XS_COUNTER_WORD and XS_COUNTER_WORD + 1 of that
+// block are the work counters of k_xspec_tc (next run, CTAs finished).  They
+// are zero between launches: the kernel's last CTA resets them, so launches on
+// one stream (and graph replays) may share the block.
+constexpr int XS_COUNTER_WORD = 32;
+constexpr int ERR_BLOCK_BYTES = 256;
+
 }  // namespace c2d

@@ -24,6 +24,15 @@
 //               is about to overwrite.
 // TMEM holds two accumulator sets (2 x 256 columns): the MMAs of tile i+1
 // run while the epilogue of tile i streams its stores.
+//
+// Work distribution: each CTA's first run of `chunk` list entries is its own
+// (blockIdx.x); later runs come from a counter in global memory (atomicAdd),
+// so CTAs that finish early take more tiles and all finish within about one
+// tile of each other.  The producer reads each run one run ahead and publishes
+// every tile to the MMA thread and the epilogue warps through a ring of
+// XS_SCHED shared-memory slots (sfull / sempty barriers); a slot holding
+// prob < 0 ends the loop.  The last CTA to finish resets the counter for the
+// next launch (graph replays included).
 #include "internal.h"
 #include "ptx.cuh"
 
@@ -36,9 +45,17 @@ constexpr int XS_BOX_BYTES = 32 * 32 * 4;
 constexpr int XS_EPI_SLOTS = 2;                   // staging boxes per epilogue warp (ring)
 static_assert(XS_EPI_SLOTS >= 2, "a box and its mirror need two staging slots");
 constexpr int XS_THREADS = 64 + 32 * XS_EPI_WARPS;
+constexpr int XS_SCHED = 8;  // tile-schedule ring slots (> the tiles the producer runs ahead)
+static_assert((XS_SCHED & (XS_SCHED - 1)) == 0 && XS_SCHED > XS_STAGES,
+              "the schedule ring must outrun the operand ring");
+// barriers (full/empty per stage, tfull/tempty per TMEM buffer, sfull/sempty
+// per schedule slot), the TMEM base address, then the schedule ring
+constexpr int XS_NBARS = 2 * XS_STAGES + 4 + 2 * XS_SCHED;
+constexpr size_t XS_CTRL = 512;
+static_assert(XS_NBARS * 8 + 8 + (XS_SCHED + 1) * sizeof(XItem) <= XS_CTRL, "control block");
 constexpr size_t XS_SMEM = 1024 + (size_t)XS_STAGES * XS_STAGE_BYTES +
                            (size_t)XS_EPI_WARPS * XS_EPI_SLOTS * XS_BOX_BYTES +
-                           (size_t)2 * TILE_N * 4 + 256;
+                           (size_t)2 * TILE_N * 4 + XS_CTRL;
 
 // Accumulation order.  Tensor-core FP32 accumulation truncates each addition,
 // so its error grows with the number of MMAs added while the accumulator is
@@ -78,11 +95,22 @@ __device__ __forceinline__ void issue_chunk_mmas(uint32_t d_phi, uint32_t d_psi,
   }
 }
 
-// The k-th work item of this CTA: runs of `chunk` consecutive list entries,
-// one run every gridDim.x * chunk entries (monotonic in k).  chunk > 1 keeps
-// a CTA on one problem for several tiles in a batch of small problems.
-__device__ __forceinline__ int item_at(int k, int chunk) {
-  return (k / chunk) * (int)gridDim.x * chunk + (int)blockIdx.x * chunk + (k % chunk);
+// Runs of `chunk` consecutive list entries: the first run of a CTA starts at
+// blockIdx.x * chunk, the later ones at gridDim.x * chunk + (the counter's old
+// value), the counter advancing by chunk per run.  chunk > 1 keeps a CTA on
+// one problem for several tiles in a batch of small problems.
+__device__ __forceinline__ int next_run(int* ctr, int chunk) {
+  return (int)gridDim.x * chunk + atomicAdd(ctr, chunk);
+}
+
+// A tile published in the schedule ring (read after its sfull barrier).
+__device__ __forceinline__ XItem read_sched(const XItem* p) {
+  const volatile XItem* v = p;
+  XItem w;
+  w.prob = v->prob;
+  w.ti = v->ti;
+  w.tj = v->tj;
+  return w;
 }
 
 template <int P>
@@ -95,16 +123,33 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
   uint8_t* epi = base + XS_STAGES * XS_STAGE_BYTES;
   float* s2stage = (float*)(epi + XS_EPI_WARPS * XS_EPI_SLOTS * XS_BOX_BYTES);
   uint64_t* bars = (uint64_t*)(s2stage + 2 * TILE_N);
-  // bars: full[S], empty[S], tfull[2], tempty[2]
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * XS_STAGES + 4);
+  // bars: full[S], empty[S], tfull[2], tempty[2], sfull[R], sempty[R]
+  uint32_t* tmem_slot = (uint32_t*)(bars + XS_NBARS);
+  XItem* sched = (XItem*)(tmem_slot + 2);  // schedule ring (8-byte aligned)
+  XItem* first_sm = sched + XS_SCHED;      // this CTA's first tile
   auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
   auto empty_bar = [&](int s) { return smem_u32(&bars[XS_STAGES + s]); };
   auto tfull_bar = [&](int b) { return smem_u32(&bars[2 * XS_STAGES + b]); };
   auto tempty_bar = [&](int b) { return smem_u32(&bars[2 * XS_STAGES + 2 + b]); };
+  auto sfull_bar = [&](int r) { return smem_u32(&bars[2 * XS_STAGES + 4 + r]); };
+  auto sempty_bar = [&](int r) { return smem_u32(&bars[2 * XS_STAGES + 4 + XS_SCHED + r]); };
+  int* ctr = err + XS_COUNTER_WORD;  // [0] next run, [1] CTAs finished
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const WaitCtl wc{err, limit_ns};
 
+  // The first tile is known now: an epilogue warp fetches it and warms the TMA
+  // unit's descriptor cache while thread 0 sets up the barriers and warp 1 TMEM.
+  const int first_it = (int)blockIdx.x * chunk;
+  if (threadIdx.x == 64) {
+    XItem f{-1, 0, 0};
+    if (first_it < nitems) {
+      f = items[first_it];
+      tma_prefetch_desc(&probs[f.prob].tmA);
+      tma_prefetch_desc(&probs[f.prob].tmB);
+    }
+    *first_sm = f;
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < XS_STAGES; ++s) {
       mbar_init(full_bar(s), 1);
@@ -113,6 +158,10 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
       mbar_init(tempty_bar(b), XS_EPI_WARPS);
+    }
+    for (int r = 0; r < XS_SCHED; ++r) {
+      mbar_init(sfull_bar(r), 1);
+      mbar_init(sempty_bar(r), 1 + XS_EPI_WARPS);  // the MMA thread and every epilogue warp
     }
     fence_barrier_init();
   }
@@ -138,10 +187,28 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
       bool ok = (inject & 1) == 0;
       const uint64_t keep = l2_policy_evict_last();  // operand rows are re-read by every CTA
       int cur_prob = -1, nch = 0, bn = 0;
-      for (int k = 0; ok; ++k) {
-        const int it = item_at(k, chunk);
-        if (it >= nitems) break;
-        const XItem w = items[it];
+      // current run [run, run + chunk) and the next one, read a run ahead
+      int run = first_it, pos = 0;
+      int ahead = (ok && run < nitems) ? next_run(ctr, chunk) : nitems;
+      XItem w = *first_sm;
+      for (int lt = 0; ok; ++lt) {
+        // this tile: the next entry of the current run, else of the next run
+        int it = run + pos;
+        if (pos == chunk || it >= nitems) {
+          run = ahead;
+          pos = 0;
+          it = run;
+          if (run < nitems) ahead = next_run(ctr, chunk);
+        }
+        const bool done = it >= nitems;
+        if (!done && lt > 0) w = items[it];
+        ++pos;
+        // publish it (prob < 0 ends the other roles' loops)
+        const int ss = lt & (XS_SCHED - 1);
+        if (!mbar_wait(sempty_bar(ss), ((uint32_t)(lt / XS_SCHED) & 1u) ^ 1u, wc)) break;
+        sched[ss] = done ? XItem{-1, 0, 0} : w;
+        mbar_arrive(sfull_bar(ss));
+        if (done) break;
         const XProblem* pr = probs + w.prob;
         if (w.prob != cur_prob) {
           cur_prob = w.prob;
@@ -149,7 +216,7 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
           bn = pr->bn;
         }
         {  // warm the TMA unit's descriptor cache for the next problem
-          const int nx = item_at(k + 1, chunk);
+          const int nx = (pos < chunk && it + 1 < nitems) ? it + 1 : ahead;
           if (nx < nitems) {
             const int np = items[nx].prob;
             if (np != w.prob) {
@@ -184,10 +251,12 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
       bool ok = true;
       int cur_prob = -1, nch = 0;
       uint32_t id = 0, idn = 0;
-      for (int k = 0; ok; ++k, ++lt) {
-        const int it = item_at(k, chunk);
-        if (it >= nitems) break;
-        const XItem w = items[it];
+      for (;; ++lt) {
+        const int ss = lt & (XS_SCHED - 1);
+        if (!mbar_wait(sfull_bar(ss), (uint32_t)(lt / XS_SCHED) & 1u, wc)) { ok = false; break; }
+        const XItem w = read_sched(sched + ss);
+        mbar_arrive(sempty_bar(ss));
+        if (w.prob < 0) break;
         if (w.prob != cur_prob) {
           cur_prob = w.prob;
           nch = probs[w.prob].nchunks;
@@ -234,10 +303,13 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
     const float* s2p = nullptr;
     int n1 = 0, n2 = 0, bn = 0, pmirror = 0, orow_off = 0, upper = 0;
     float norm = 0.f;
-    for (int k = 0;; ++k, ++lt) {
-      const int it = item_at(k, chunk);
-      if (it >= nitems) break;
-      const XItem w = items[it];
+    for (;; ++lt) {
+      const int ss = lt & (XS_SCHED - 1);
+      if (!mbar_wait(sfull_bar(ss), (uint32_t)(lt / XS_SCHED) & 1u, wc)) break;
+      const XItem w = read_sched(sched + ss);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(sempty_bar(ss));
+      if (w.prob < 0) break;
       if (w.prob != cur_prob) {
         cur_prob = w.prob;
         const XProblem* pr = probs + w.prob;
@@ -368,6 +440,16 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
   tc_fence_before();
   __syncthreads();
   if (warp == 1) tmem_dealloc(tmem, 512);
+  // every role of this CTA has stopped taking runs: count the CTA as finished;
+  // the last one resets the counters for the next launch on this stream
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(ctr + 1, 1) == (int)gridDim.x - 1) {
+      ctr[0] = 0;
+      ctr[1] = 0;
+      __threadfence();
+    }
+  }
 }
 
 static_assert(XS_SMEM <= (size_t)kMaxDynSmem, "cross-spectrum shared memory exceeds the limit");

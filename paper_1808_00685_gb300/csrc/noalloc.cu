@@ -205,7 +205,7 @@ extern "C" corr2d_status corr2d_compute_noalloc(int device, void* cuda_stream, i
   const long nitems = mirror ? (long)nt1 * (nt1 + 1) / 2 : (long)nt1 * nt2;
   const int njobs = shared_rows ? 1 : 2;
   const int npitems = nt1 + (shared_rows ? 0 : (n2 + PREP_ROWS - 1) / PREP_ROWS);
-  size_t off = 256;  // error word
+  size_t off = ERR_BLOCK_BYTES;  // error word and the cross-spectrum work counters
   const size_t off_tw = off; off = up(off + tw_bytes, 1024);
   const size_t off_tw2 = off; off = up(off + tw2_bytes, 1024);
   const size_t off_a = off;  off = up(off + (size_t)n1 * rowlen * 2, 1024);
@@ -298,8 +298,9 @@ extern "C" corr2d_status corr2d_compute_noalloc(int device, void* cuda_stream, i
   for (int ti = 0; ti < nt1; ++ti)
     for (int tj = mirror ? ti : 0; tj < nt2; ++tj) items.push_back(XItem{0, (uint16_t)ti, (uint16_t)tj});
 
-  // ---- enqueue: the error word starts at zero; the rest is written before it is read
-  cudaError_t e = cudaMemsetAsync(S, 0, 256, stream);
+  // ---- enqueue: the error word and the work counters start at zero; the rest
+  // is written before it is read
+  cudaError_t e = cudaMemsetAsync(S, 0, ERR_BLOCK_BYTES, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S + off_tw, tw.data(), tw_bytes, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess && hilbert)
     e = cudaMemcpyAsync(S + off_tw2, tw2.data(), tw2_bytes, cudaMemcpyHostToDevice, stream);
