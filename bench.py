@@ -18,9 +18,12 @@ runs.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload c4|c2|c3|c5] [--precision split|bf16|fp32]
 
-Under torchrun each rank runs its own independent problem on its own GPU
-(weak scaling, no data-path collective); the reported value is all ranks'
-outputs divided by the slowest rank's time.  --impl reference times the FP64
+Under torchrun the homo workloads (c4, c2) are split over the ranks by output
+tiles (corr2d_compute_part: each GPU a balanced, contiguous part of the
+mirrored tile list, written into its own buffer; strong scaling, no data-path
+collective): the value is the problem's outputs divided by the slowest rank's
+time.  The other workloads run one independent problem per rank (weak
+scaling): all ranks' outputs divided by the slowest rank's time.  --impl reference times the FP64
 CPU oracle on the host cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -621,6 +624,8 @@ def run_ours(args, world, rank, local, pg):
     launches_per_step = 2
     per_call_timing = True  # the step is one library call: its kernel events time it
     upper = args.upper_triangle and args.workload in ("c4", "c2")
+    strong = world > 1 and args.workload in ("c4", "c2") and args.precision != "fp32"
+    scaling, parallelism = "weak", None
 
     if args.workload in ("c4", "c2"):
         y, _ = inputs
@@ -628,12 +633,27 @@ def run_ours(args, world, rank, local, pg):
         m, n = y.shape
         phi, psi, ldo = pkg.Context.alloc_out(n, n, device)
         outputs = n * n
-
-        def step():
-            ctx.compute(yd, precision=args.precision, out=(phi, psi), upper_triangle=upper)
         # Phi and Psi stored (the upper triangle only: n (n + 1) / 2 pairs), the homo
         # problem's one operand row set read once
         stored = n * (n + 1) / 2 if upper else n * n
+        if strong:
+            # this rank's part of the mirrored tile list: its blocks and mirrored blocks
+            tiles = pkg.corr2d_plan_part(n, n, True, 0, rank, world)
+            stored = 0.0
+            for ti, tj in tiles:
+                area = min(128, n - 128 * ti) * min(128, n - 128 * tj)
+                stored += area * (1 if (upper or ti == tj) else 2)
+            scaling = "strong"
+            parallelism = (f"strong: one problem split by output tiles over {world} GPUs "
+                           f"(corr2d_compute_part, balanced parts of the mirrored tile list; "
+                           f"this rank {len(tiles)} tiles), no collective")
+
+            def step():
+                ctx.compute_part(yd, None, rank, world, precision=args.precision,
+                                 upper_triangle=upper, out=(phi, psi))
+        else:
+            def step():
+                ctx.compute(yd, precision=args.precision, out=(phi, psi), upper_triangle=upper)
         xbytes = 8.0 * stored + 1.0 * n * rowlen_elems(m, args.precision) * 2
         if upper:
             desc["workload"] += " upper triangle"
@@ -698,7 +718,7 @@ def run_ours(args, world, rank, local, pg):
               pkg.XSPEC_TC_TA: "k_xspec_ta", pkg.XSPEC_FP32: "k_xspec_simt"}.get(kind, "none")
     ms = statistics.mean(t["step_ms"])
     ms_max = reduce_max(pg, ms, device)
-    value = world * outputs / (ms_max / 1e3)
+    value = (1 if strong else world) * outputs / (ms_max / 1e3)
 
     peak, peak_kind = measured_peaks()
     # several calls per step: the per-kernel events cover the last call only,
@@ -735,7 +755,7 @@ def run_ours(args, world, rank, local, pg):
     # sampled outputs of the main run, for its error against the oracle
     checks = {}
     rows = cols = None
-    if args.workload in ("c4", "c2") and rank == 0:
+    if args.workload in ("c4", "c2") and rank == 0 and not strong:
         rows, cols = sample_block(n, upper)
         checks["main"] = [(y, None, rows, cols, 0.0, gather(phi, psi, rows, cols))]
 
@@ -754,7 +774,7 @@ def run_ours(args, world, rank, local, pg):
     # end to end through the host-buffer entry point (pinned host memory placed on
     # the GPU's NUMA node when sysfs names it)
     e2e = None
-    if not args.no_e2e and args.workload in ("c4", "c2"):
+    if not args.no_e2e and args.workload in ("c4", "c2") and not strong:
         node, cpus = gpu_numa_cpus(local)
         saved = os.sched_getaffinity(0)
         if cpus:
@@ -808,12 +828,12 @@ def run_ours(args, world, rank, local, pg):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": scaling, "vs_baseline": None,
         "dtype": {"split": "f16 hi/lo split, f32 accumulate (double-float f32 centering)",
                   "bf16": "bf16, f32 accumulate (double-float f32 centering)",
                   "fp32": "f32 (f64 centering)"}[args.precision],
         "data": "synthetic (seeded band spectra; the paper's datasets are not available)",
-        "config": config_for(desc, world, args.l2),
+        "config": config_for(desc, world, args.l2, parallelism),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches_per_step * args.steps,
         "region_ms": round(t["region_ms"], 3),

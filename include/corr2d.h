@@ -260,6 +260,46 @@ corr2d_status corr2d_compute_rows(corr2d_ctx* ctx, int m, int n1, const float* y
                                   long ldo);
 
 /*
+ * One part of the output tiles, for splitting one problem over several GPUs
+ * while keeping the homo mirror (the cross-spectrum of Eq. disint2d split by
+ * output tiles; the paper's own parallel scheme, Sec. 4.2, splits the matrix
+ * product over column blocks on CPU cores).  The problem's 128 x 128 output
+ * tiles are listed in a fixed order -- homo problems: mirrored tiles (nu1-block
+ * <= nu2-block, each writing itself and its transpose) in 64 x 64 super-blocks,
+ * unless CORR2D_FLAG_NO_MIRROR; hetero problems: row-major -- and the list is cut
+ * into `nparts` contiguous parts of about equal cost (a tile costs its stored
+ * 128 x 128 blocks, two for an off-diagonal mirrored tile, plus one for its
+ * tensor-core work).  This call computes part `part` (0 <= part < nparts): every
+ * tile of the part and, for mirrored tiles, its mirrored block, written at their
+ * places in the full n1 x n2 phi/psi (leading dimension ldo); nothing else of
+ * phi/psi is written.  The parts of one problem cover every output exactly
+ * once, so phi/psi of the nparts calls (one per GPU, each into its own buffer)
+ * combine by taking each element from the part that wrote it
+ * (corr2d_plan_part names the tiles).  Each call transforms both whole stacks
+ * (cheap next to its share of the output); the parts need no communication.
+ * The order is not tuned, so every process builds the same list.  Tensor-core
+ * precisions; flags as corr2d_compute (UPPER_TRIANGLE drops the mirrored
+ * blocks).  Other arguments and errors as corr2d_compute; a part with no tiles
+ * (nparts larger than the tile count) writes nothing.
+ */
+corr2d_status corr2d_compute_part(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1,
+                                  int n2, const float* y2, int ld2, const corr2d_params* params,
+                                  int part, int nparts, float* phi, float* psi, long ldo);
+
+/*
+ * Host-only companion of corr2d_compute_part (no GPU, no context): the tiles of
+ * part `part` of `nparts` of an n1 x n2 problem (homo != 0: n2 is ignored and
+ * the mirrored list is used unless `flags` holds CORR2D_FLAG_NO_MIRROR), in list
+ * order.  *count receives the number of tiles; when tiles is not NULL it
+ * receives 2 * count ints (ti, tj): tile (ti, tj) covers rows 128 ti .. and
+ * columns 128 tj .. of the map, and a mirrored tile with ti != tj also the
+ * transposed block.  EINVAL for a bad shape or part, or cap < count (tiles
+ * not NULL); corr2d_last_error(NULL) describes the failure.
+ */
+corr2d_status corr2d_plan_part(int n1, int n2, int homo, unsigned flags, int part, int nparts,
+                               int* tiles, int cap, int* count);
+
+/*
  * Same computation with every buffer in HOST memory: the library copies the
  * stacks to its device workspace, computes, and copies Phi and Psi back in
  * row slabs so that copies overlap the kernels.  Blocks until the results are

@@ -43,7 +43,8 @@ EXPORTED_SYMBOLS = (
     "corr2d_compute_host", "corr2d_batch", "corr2d_version", "corr2d_set_profiling",
     "corr2d_get_timings", "corr2d_compute_noalloc", "corr2d_preprocess_perturbation",
     "corr2d_compute_rows", "corr2d_compute_reduced", "corr2d_interpolate_perturbation",
-    "corr2d_get_kernel_info", "corr2d_measure_fp32_peak",
+    "corr2d_get_kernel_info", "corr2d_measure_fp32_peak", "corr2d_compute_part",
+    "corr2d_plan_part",
 )
 XSPEC_NONE, XSPEC_TC, XSPEC_TC_PAIR, XSPEC_FP32, XSPEC_TC_TA = range(5)
 
@@ -111,6 +112,10 @@ def load(path: str | None = None):
                                        ctypes.POINTER(ctypes.c_float)]),
             "corr2d_get_kernel_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i)]),
             "corr2d_measure_fp32_peak": (i, [vp, ctypes.POINTER(d)]),
+            "corr2d_compute_part": (i, [vp, i, i, vp, i, i, vp, i, ctypes.POINTER(corr2d_params),
+                                        i, i, vp, vp, ctypes.c_long]),
+            "corr2d_plan_part": (i, [i, i, i, ctypes.c_uint, i, i, ctypes.POINTER(i), i,
+                                     ctypes.POINTER(i)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -188,6 +193,26 @@ def corr2d_compute_reduced(ctx, m, n1, y1, ld1, n2, y2, ld2, params, reduce, phi
     pp = ctypes.byref(params) if params is not None else None
     _check(ctx, load().corr2d_compute_reduced(ctx, m, n1, y1, ld1, n2, y2, ld2, pp, reduce,
                                               phi_r, psi_r, ldr))
+
+
+def corr2d_compute_part(ctx, m, n1, y1, ld1, n2, y2, ld2, params, part, nparts, phi, psi,
+                        ldo) -> None:
+    pp = ctypes.byref(params) if params is not None else None
+    _check(ctx, load().corr2d_compute_part(ctx, m, n1, y1, ld1, n2, y2, ld2, pp, part, nparts,
+                                           phi, psi, ldo))
+
+
+def corr2d_plan_part(n1: int, n2: int, homo: bool, flags: int, part: int, nparts: int):
+    """Tiles (ti, tj) of part `part` of `nparts` of an n1 x n2 problem, in list order
+    (host only; the tile split corr2d_compute_part uses)."""
+    lib = load()
+    cnt = ctypes.c_int()
+    _check(None, lib.corr2d_plan_part(n1, n2, 1 if homo else 0, flags, part, nparts, None, 0,
+                                      ctypes.byref(cnt)))
+    buf = (ctypes.c_int * max(2 * cnt.value, 1))()
+    _check(None, lib.corr2d_plan_part(n1, n2, 1 if homo else 0, flags, part, nparts, buf,
+                                      cnt.value, ctypes.byref(cnt)))
+    return [(buf[2 * i], buf[2 * i + 1]) for i in range(cnt.value)]
 
 
 def shard_rows(n1: int, world: int, rank: int, tile: int = 128):
@@ -440,6 +465,24 @@ class Context:
         params = make_params(precision, alpha, norm, hilbert=hilbert)
         corr2d_compute_rows(self.handle, m, n1, _ptr(y1), y1.stride(0), n2, _ptr(y2),
                             y2.stride(0) if y2 is not None else 0, params, row_begin, row_count,
+                            _ptr(phi), _ptr(psi), ldo)
+        return phi[:, :n2], psi[:, :n2]
+
+    def compute_part(self, y1, y2, part, nparts, precision="split", alpha=0.0, norm=0.0,
+                     no_mirror=False, upper_triangle=False, out=None):
+        """Part `part` of `nparts` of the output tiles (and their mirrors) of Phi and Psi,
+        written at their places in full n1 x n2 buffers; other elements are untouched."""
+        m, n1 = y1.shape
+        n2 = n1 if y2 is None else y2.shape[1]
+        if out is None:
+            phi, psi, ldo = self.alloc_out(n1, n2, y1.device)
+        else:
+            phi, psi = out
+            ldo = phi.stride(0)
+        params = make_params(precision, alpha, norm, no_mirror=no_mirror,
+                             upper_triangle=upper_triangle)
+        corr2d_compute_part(self.handle, m, n1, _ptr(y1), y1.stride(0), n2, _ptr(y2),
+                            y2.stride(0) if y2 is not None else 0, params, part, nparts,
                             _ptr(phi), _ptr(psi), ldo)
         return phi[:, :n2], psi[:, :n2]
 

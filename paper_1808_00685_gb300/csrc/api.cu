@@ -293,6 +293,40 @@ void append_tiles(std::vector<XItem>& items, int prob, int n1, int n2, int bn, b
           items.push_back(XItem{prob, (uint16_t)ti, (uint16_t)tj});
 }
 
+// Tile order of corr2d_compute_part / corr2d_plan_part: fixed (not tuned), so
+// that every process splitting one problem builds the same list: homo problems
+// mirrored in 64 x 64 super-blocks (the order the tuner takes for the large homo
+// workloads), unless NO_MIRROR; hetero problems row-major.
+constexpr int kPartGroup = 64;
+
+// Part `part` of `nparts` of a problem's tile list (128 x 128 tiles): the
+// list cut into contiguous ranges of about equal cost, a tile costing its
+// stored blocks (area / 128^2; an off-diagonal mirrored tile stores two) plus
+// one for its MMA and operand work.  Tile i goes to the part containing the
+// middle of its cost interval, so every tile lands in exactly one part and the
+// parts are consecutive in list order (they keep the super-block locality).
+void part_tiles(std::vector<XItem>& out, int prob, int n1, int n2, bool mirror, int part,
+                int nparts) {
+  std::vector<XItem> all;
+  append_tiles(all, prob, n1, n2, TILE_N, mirror, 0, (n1 + TILE_M - 1) / TILE_M,
+               mirror ? kPartGroup : 0);
+  std::vector<double> w(all.size());
+  double total = 0.0;
+  for (size_t i = 0; i < all.size(); ++i) {
+    const double rows = std::min(TILE_M, n1 - (int)all[i].ti * TILE_M);
+    const double cols = std::min(TILE_N, n2 - (int)all[i].tj * TILE_N);
+    const double area = rows * cols / (double)(TILE_M * TILE_N);
+    w[i] = 1.0 + ((mirror && all[i].ti != all[i].tj) ? 2.0 * area : area);
+    total += w[i];
+  }
+  double cum = 0.0;
+  for (size_t i = 0; i < all.size(); ++i) {
+    const int p = std::min(nparts - 1, (int)((cum + 0.5 * w[i]) * nparts / total));
+    cum += w[i];
+    if (p == part) out.push_back(all[i]);
+  }
+}
+
 // Item list of the CTA-pair kernel: ti indexes pairs of 128-row tiles (rows
 // 256 ti .. 256 ti + 255), tj 128-column tiles.  Mirrored problems take the
 // items with tj >= 2 ti, which cover every tile on or above the diagonal once.
@@ -409,7 +443,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
                          const TileChoice& tc, int ti_begin, int ti_end, int out_row_tile0,
                          bool skip_prep, DevBuf& opsbuf, DevBuf& descbuf,
                          std::vector<uint8_t>& desc_last, bool cached = false,
-                         int cstride = 1) {
+                         int cstride = 1, int part = 0, int nparts = 1) {
   const bool homo = (y2 == nullptr);
   const bool hilbert = (p.flags & CORR2D_FLAG_HILBERT) != 0;
   TcPlan pl = plan_tc(m, n1, n2, homo, p.precision, hilbert);
@@ -461,7 +495,8 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
     const void* ptrs[] = {y1, y2, phi, psi, sig1, sig2, p.ref1, p.ref2, opsbuf.p};
     const int ints[] = {m, n1, ld1, n2, ld2, out_rows, p.ref_mode, p.precision, (int)p.flags,
                         tc.bn, tc.mirror, tc.group, ti_begin, ti_end, out_row_tile0,
-                        skip_prep ? 1 : 0, cstride, tc.pair, tc.chunk, tc.ta, tc.stages};
+                        skip_prep ? 1 : 0, cstride, tc.pair, tc.chunk, tc.ta, tc.stages,
+                        part, nparts};
     put(ptrs, sizeof ptrs);
     put(ints, sizeof ints);
     put(&ldo, sizeof ldo);
@@ -511,12 +546,12 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
     mkjob(y2, ld2, n2, r2, nullptr, opB, s2, sig2, hilbert ? wtab_b : wtab);
   }
   // the CTA-pair kernel computes whole 256-row pairs of tiles with bn = 128
-  const bool pair = tc.pair && tc.bn == TILE_N && ti_begin == 0 &&
+  const bool pair = nparts == 1 && tc.pair && tc.bn == TILE_N && ti_begin == 0 &&
                     ti_end == (n1 + TILE_M - 1) / TILE_M && out_row_tile0 == 0 &&
                     ctx->pair_clusters > 0;
   // the TMEM-operand kernel holds a row's stack-1 chunks in TMEM (at most
   // TA_MAX_CHUNKS) and also computes whole problems
-  const bool ta = tc.ta > 0 && !pair && pl.nch <= TA_MAX_CHUNKS && ti_begin == 0 &&
+  const bool ta = nparts == 1 && tc.ta > 0 && !pair && pl.nch <= TA_MAX_CHUNKS && ti_begin == 0 &&
                   ti_end == (n1 + TILE_M - 1) / TILE_M && out_row_tile0 == 0;
   const int bn = ta ? TILE_N : tc.bn;
   XProblem xp;
@@ -544,6 +579,8 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
     append_segments(segs, 0, n1, n2, xp.mirror != 0, tc.ta);
   else if (pair)
     append_pair_tiles(xitems, 0, n1, n2, xp.mirror != 0, tc.group);
+  else if (nparts > 1)
+    part_tiles(xitems, 0, n1, n2, xp.mirror != 0, part, nparts);
   else
     append_tiles(xitems, 0, n1, n2, tc.bn, xp.mirror != 0, ti_begin, ti_end, tc.group);
   Blob b = ta ? pack(skip_prep ? std::vector<PrepJob>{} : jobs,
@@ -1170,6 +1207,56 @@ corr2d_status corr2d_compute_rows(corr2d_ctx* ctx, int m, int n1, const float* y
   const int t0 = row_begin / TILE_M, t1 = (row_begin + row_count + TILE_M - 1) / TILE_M;
   st = enqueue_tc(ctx, m, n1, y1, ld1, n2, homo ? nullptr : y2, ld2, p, phi, psi, ldo, row_count,
                   nullptr, nullptr, tc, t0, t1, t0, false, ctx->ops, ctx->desc, ctx->desc_host);
+  if (st != CORR2D_OK) return st;
+  ctx->err.clear();
+  return CORR2D_OK;
+}
+
+corr2d_status corr2d_plan_part(int n1, int n2, int homo, unsigned flags, int part, int nparts,
+                               int* tiles, int cap, int* count) {
+  if (!count) return fail(nullptr, CORR2D_EINVAL, "count is NULL");
+  *count = 0;
+  if (homo) n2 = n1;
+  if (n1 < 1 || n2 < 1) return fail(nullptr, CORR2D_EINVAL, "n1 and n2 must be >= 1");
+  if (nparts < 1 || part < 0 || part >= nparts)
+    return fail(nullptr, CORR2D_EINVAL, "part %d of %d is not a part", part, nparts);
+  if ((long)(n1 + TILE_M - 1) / TILE_M > 65535 || (long)(n2 + TILE_N - 1) / TILE_N > 65535)
+    return fail(nullptr, CORR2D_EUNSUPPORTED, "n too large for the tile index");
+  std::vector<XItem> v;
+  part_tiles(v, 0, n1, n2, homo && !(flags & CORR2D_FLAG_NO_MIRROR), part, nparts);
+  *count = (int)v.size();
+  if (tiles) {
+    if (cap < (int)v.size())
+      return fail(nullptr, CORR2D_EINVAL, "part %d has %d tiles; cap is %d", part, (int)v.size(),
+                  cap);
+    for (size_t i = 0; i < v.size(); ++i) {
+      tiles[2 * i] = v[i].ti;
+      tiles[2 * i + 1] = v[i].tj;
+    }
+  }
+  return CORR2D_OK;
+}
+
+corr2d_status corr2d_compute_part(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1,
+                                  int n2, const float* y2, int ld2, const corr2d_params* params,
+                                  int part, int nparts, float* phi, float* psi, long ldo) {
+  if (!ctx) return CORR2D_EINVAL;
+  corr2d_params p;
+  if (params) p = *params; else corr2d_params_default(&p);
+  DeviceGuard g(ctx->device);
+  corr2d_status st = validate_compute(ctx, m, n1, y1, ld1, n2, y2, ld2, p, phi, psi, ldo, true);
+  if (st != CORR2D_OK) return st;
+  if (p.precision == CORR2D_PREC_FP32)
+    return fail(ctx, CORR2D_EUNSUPPORTED, "parts run the tensor-core precisions");
+  if (nparts < 1 || part < 0 || part >= nparts)
+    return fail(ctx, CORR2D_EINVAL, "part %d of %d is not a part", part, nparts);
+  const bool homo = (y2 == nullptr);
+  if (homo) { n2 = n1; ld2 = ld1; }
+  const bool mirror = homo && !(p.flags & CORR2D_FLAG_NO_MIRROR);
+  TileChoice tc{128, mirror ? 1 : 0, mirror ? kPartGroup : 0};
+  st = enqueue_tc(ctx, m, n1, y1, ld1, n2, homo ? nullptr : y2, ld2, p, phi, psi, ldo, n1,
+                  nullptr, nullptr, tc, 0, (n1 + TILE_M - 1) / TILE_M, 0, false, ctx->ops,
+                  ctx->desc, ctx->desc_host, true, 1, part, nparts);
   if (st != CORR2D_OK) return st;
   ctx->err.clear();
   return CORR2D_OK;

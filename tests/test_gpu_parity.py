@@ -363,6 +363,32 @@ def test_preprocess_reference_subtraction_bit_exact(ctx):
     assert np.array_equal(dyn.cpu().numpy(), od.astype(np.float32))
 
 
+@pytest.mark.parametrize("kind,m,n_raw,n_out", [("exponential", 7, 900, 640),
+                                                 ("clustered", 33, 2000, 3000),
+                                                 ("two points", 1, 2, 17),
+                                                 ("one row", 1, 500, 123)])
+def test_preprocess_on_non_uniform_axes_bit_exact(ctx, kind, m, n_raw, n_out):
+    """The segment search starts from the equally spaced estimate and gallops: axes
+    far from equal spacing (exponential, clustered) and the smallest shapes must
+    give the oracle's values bit for bit."""
+    rng = np.random.default_rng(n_raw)
+    if kind == "exponential":
+        x = np.exp(np.linspace(0.0, 9.0, n_raw))
+    elif kind == "clustered":
+        x = np.cumsum(rng.exponential(1.0, n_raw) ** 3 + 1e-6)
+    else:
+        x = np.sort(rng.uniform(-5.0, 5.0, n_raw))
+    x = np.unique(x)
+    assert len(x) == n_raw
+    y = workloads.random_stack(m, n_raw, seed=n_out, offset=1.0)
+    ref = workloads.random_stack(1, n_out, seed=n_out + 1)[0]
+    out, dyn = ctx.preprocess(dev(x), dev(y), n_out, ref=dev(ref))
+    ctx.synchronize()
+    o, od = oracle.interp_linear(x, y, n_out, ref=ref)
+    assert np.array_equal(out.cpu().numpy(), o.astype(np.float32))
+    assert np.array_equal(dyn.cpu().numpy(), od.astype(np.float32))
+
+
 def test_preprocess_rejects_non_increasing_axis(ctx):
     import paper_1808_00685_gb300 as pkg
     x = np.linspace(0, 1, 50)
@@ -615,6 +641,42 @@ def test_row_slabs_assemble_the_full_result(ctx):
         check(phi, psi, ophi, opsi, 1e-5, f"{world} row slabs")
     with pytest.raises(pkg.Corr2dError):
         ctx.compute_rows(d1, d2, 100, 10)  # not a multiple of 128
+
+
+@pytest.mark.parametrize("homo", [True, False])
+def test_tile_parts_assemble_the_full_result(ctx, homo):
+    """Multi-GPU split of one problem on one GPU: each part (one per would-be GPU)
+    written into its own NaN-filled buffers; every element is written by exactly one
+    part, and the parts together equal the oracle (homo: exactly (anti)symmetric,
+    since the parts keep the mirror)."""
+    import paper_1808_00685_gb300 as pkg
+    n1 = 900
+    y1 = workloads.random_stack(40, n1, seed=81, offset=1.0)
+    y2 = None if homo else workloads.random_stack(40, 333, seed=82, offset=-2.0)
+    n2 = n1 if homo else 333
+    d1 = dev(y1)
+    d2 = None if homo else dev(y2)
+    ophi, opsi, _, _ = oracle.corr2d(y1, y2)
+    for nparts in (1, 2, 3, 5):
+        got_phi, got_psi = [], []
+        for part in range(nparts):
+            phi, psi, _ = pkg.Context.alloc_out(n1, n2, d1.device)
+            phi.fill_(float("nan"))
+            psi.fill_(float("nan"))
+            ph, ps = ctx.compute_part(d1, d2, part, nparts, out=(phi, psi))
+            ctx.synchronize()
+            got_phi.append(host(ph))
+            got_psi.append(host(ps))
+        wp = np.stack([~np.isnan(a) for a in got_phi])
+        wq = np.stack([~np.isnan(a) for a in got_psi])
+        assert np.all(wp.sum(0) == 1) and np.all(wq.sum(0) == 1), f"{nparts} parts overlap or leave gaps"
+        phi = np.where(wp, np.stack(got_phi), 0.0).sum(0)
+        psi = np.where(wq, np.stack(got_psi), 0.0).sum(0)
+        check(phi, psi, ophi, opsi, 1e-5, f"{nparts} tile parts homo={homo}")
+        if homo:
+            assert np.array_equal(phi, phi.T) and np.array_equal(psi, -psi.T)
+    with pytest.raises(pkg.Corr2dError):
+        ctx.compute_part(d1, d2, 3, 3)
 
 
 def test_upper_triangle_output(ctx):

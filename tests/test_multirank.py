@@ -1,8 +1,13 @@
-"""Multi-process (world size 2, gloo on CPU) coverage of the benchmark's rank logic.
+"""Multi-process (world size 2, gloo on CPU) coverage of the multi-GPU logic.
 
-The correlation shards by independent problems: each rank runs its own problem
-and the only cross-rank operations are the timing barrier and the max-over-ranks
-reduction.  These run here without a GPU."""
+Two ways to use several GPUs: independent problems per rank (the only
+cross-rank operations are the timing barrier and the max-over-ranks
+reduction), and one problem split by output tiles (corr2d_compute_part: each
+rank computes a balanced, contiguous part of the mirrored tile list and its
+mirrored blocks; the parts cover the map exactly once).  The partition is host
+logic (corr2d_plan_part), so it is checked here without a GPU: coverage for
+many shapes, and two gloo ranks that compute their parts with the oracle and
+gather the full map."""
 import json
 import os
 import subprocess
@@ -59,3 +64,99 @@ def test_row_shards_cover_every_row_once():
                 assert r0 % 128 == 0 or cnt == 0
                 rows.extend(range(r0, r0 + cnt))
             assert rows == list(range(n1))
+
+
+# ------------------------------------------------------- tile parts (one problem)
+
+def _lib():
+    import paper_1808_00685_gb300 as pkg
+    pkg.load(pkg.build())
+    return pkg
+
+
+def _written(n1, n2, homo, tiles, mirror=True):
+    """Boolean map of the outputs a part writes: each tile's block and, for an
+    off-diagonal mirrored tile, the transposed block (a diagonal tile writes its
+    whole block: its upper triangle and the mirror of it)."""
+    import numpy as np
+    w = np.zeros((n1, n2), np.int32)
+    for ti, tj in tiles:
+        w[ti * 128:(ti + 1) * 128, tj * 128:(tj + 1) * 128] += 1
+        if homo and mirror and ti != tj:
+            w[tj * 128:(tj + 1) * 128, ti * 128:(ti + 1) * 128] += 1
+    return w
+
+
+@pytest.mark.parametrize("n1,n2,homo", [(700, 700, True), (128, 128, True), (129, 129, True),
+                                        (1000, 333, False), (4096, 4096, True)])
+@pytest.mark.parametrize("nparts", [1, 2, 3, 5, 8])
+def test_tile_parts_write_every_output_exactly_once(n1, n2, homo, nparts):
+    """corr2d_plan_part (host only): the parts are disjoint, their blocks and mirrored
+    blocks cover the n1 x n2 map exactly once, and their costs are balanced."""
+    import numpy as np
+    pkg = _lib()
+    total = np.zeros((n1, n2), np.int32)
+    costs = []
+    for part in range(nparts):
+        tiles = pkg.corr2d_plan_part(n1, n2, homo, 0, part, nparts)
+        total += _written(n1, n2, homo, tiles)
+        costs.append(sum(1 + (2 if homo and a != b else 1) for a, b in tiles))
+    assert np.all(total == 1)
+    nt = len(pkg.corr2d_plan_part(n1, n2, homo, 0, 0, 1))
+    if nt >= 8 * nparts:  # balanced to within a few tiles' cost
+        assert max(costs) - min(costs) <= 8
+    # NO_MIRROR: every tile of the map, no mirrored blocks
+    tiles = sum((pkg.corr2d_plan_part(n1, n2, homo, pkg.FLAG_NO_MIRROR, p, nparts)
+                 for p in range(nparts)), [])
+    assert np.all(_written(n1, n2, homo, tiles, mirror=False) == 1)
+
+
+def _part_worker(rank, world, port, out):
+    """One rank: its share of the tiles of a homo problem, each tile's block computed
+    by the oracle from the stacks' columns of that block (every step before the
+    cross product acts on one spectral variable at a time) and its mirror from the
+    symmetry Phi(nu2, nu1) = Phi(nu1, nu2), Psi(nu2, nu1) = -Psi(nu1, nu2); the ranks'
+    maps are gathered with gloo and rank 0 checks them against one full oracle call."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import oracle
+    import paper_1808_00685_gb300 as pkg
+    import workloads
+    pkg.load()
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    n, m = 300, 9
+    y = workloads.random_stack(m, n, seed=77, offset=2.0)
+    phi = np.full((n, n), np.nan)
+    psi = np.full((n, n), np.nan)
+    for ti, tj in pkg.corr2d_plan_part(n, n, True, 0, rank, world):
+        r = np.arange(ti * 128, min(n, ti * 128 + 128))
+        c = np.arange(tj * 128, min(n, tj * 128 + 128))
+        bp, bq, _, _ = oracle.corr2d(np.ascontiguousarray(y[:, r]), np.ascontiguousarray(y[:, c]))
+        phi[np.ix_(r, c)] = bp
+        psi[np.ix_(r, c)] = bq
+        if ti != tj:
+            phi[np.ix_(c, r)] = bp.T
+            psi[np.ix_(c, r)] = -bq.T
+    parts = [torch.zeros((2, n, n), dtype=torch.float64) for _ in range(world)]
+    dist.all_gather(parts, torch.from_numpy(np.stack([phi, psi])))
+    if rank == 0:
+        got = np.stack([p.numpy() for p in parts])  # world x 2 x n x n
+        written = ~np.isnan(got)
+        ok_once = bool(np.all(written.sum(axis=0) == 1))
+        full = np.where(written, got, 0.0).sum(axis=0)
+        ophi, opsi, _, _ = oracle.corr2d(y)
+        with open(os.path.join(out, "result.txt"), "w") as f:
+            f.write(repr((ok_once, bool(np.array_equal(full[0], ophi)),
+                          bool(np.array_equal(full[1], opsi)))))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_compute_their_tile_parts_and_gather_the_full_map(tmp_path):
+    import torch.multiprocessing as mp
+    _lib()
+    mp.spawn(_part_worker, args=(2, 29517, str(tmp_path)), nprocs=2, join=True)
+    assert open(tmp_path / "result.txt").read() == repr((True, True, True))
