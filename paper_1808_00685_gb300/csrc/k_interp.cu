@@ -3,19 +3,18 @@
 // evaluated through an interpolating function), here linear and applied along
 // the spectral axis, followed by reference subtraction (Eq. dynspec).
 //
-// One thread per output grid point and 16-row slab of the stack: it locates
-// its segment of the raw axis by binary search (FP64), then blends the two
-// neighbouring raw values of each row in FP64 with explicitly rounded
-// operations, so each output is the correctly rounded FP32 value of the plain
-// double formula.  A separate pass checks that
-// the raw axis is strictly increasing and raises the context's error word if
-// it is not.  HBM-bound: reads m x n_raw, writes m x n_out (twice with a
-// reference).
+// One thread per output grid point and slab of rows: it locates its segment
+// of the raw axis (FP64: a galloping search from where an equally spaced axis
+// would put the point), then blends the two neighbouring raw values of each row
+// in FP64 with explicitly rounded operations, so each output is the correctly
+// rounded FP32 value of the plain double formula.  The same launch checks that
+// the raw axis is strictly increasing and finite (raising the context's error
+// word if not).  Slabs get fewer rows on small grids so that the launch fills
+// the GPU.  Bound by the FP64 pipe (about six FP64 operations per output) on
+// large grids; reads m x n_raw, writes m x n_out (twice with a reference).
 #include "internal.h"
 
 namespace c2d {
-
-constexpr int INTERP_ROWS = 16;
 
 __global__ void k_check_axis(int n_raw, const double* __restrict__ x, int* err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -25,30 +24,68 @@ __global__ void k_check_axis(int n_raw, const double* __restrict__ x, int* err) 
   }
 }
 
+// Segment s of grid value xk: the largest index in [0, n_raw - 2] with
+// x[s] < xk (0 if none).  The search starts at `e` (any start gives the same
+// segment), gallops outwards to a bracket and bisects it: a few steps on
+// nearly uniform axes, O(log n_raw) on any increasing one.
+__device__ __forceinline__ int find_segment(const double* __restrict__ x, int n_raw, double xk,
+                                            int e) {
+  const int top = n_raw - 2;
+  e = e < 0 ? 0 : (e > top ? top : e);
+  int lo, hi;  // the answer lies in [lo, hi]
+  if (x[e] < xk) {
+    lo = e;
+    hi = top;
+    for (int step = 1; lo + step <= top; step <<= 1) {
+      if (x[lo + step] < xk) {
+        lo += step;
+      } else {
+        hi = lo + step - 1;
+        break;
+      }
+    }
+  } else {
+    hi = e > 0 ? e - 1 : 0;
+    lo = 0;
+    for (int step = 1; e - step > 0; step <<= 1) {
+      if (x[e - step] < xk) {
+        lo = e - step;
+        break;
+      }
+      hi = e - step - 1;
+    }
+  }
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (x[mid] < xk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(128) k_interp(int m, int n_raw, const double* __restrict__ x,
                                                 const float* __restrict__ y, int n_out,
-                                                float* __restrict__ out,
+                                                int rows_per_block, float* __restrict__ out,
                                                 const float* __restrict__ ref,
-                                                float* __restrict__ dyn) {
+                                                float* __restrict__ dyn, int* err) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.y == 0)  // the axis check, pair (i, i + 1), spread over the first slab
+    for (int i = k; i + 1 < n_raw; i += gridDim.x * blockDim.x) {
+      const double a = x[i], b = x[i + 1];
+      if (!(b > a) || !isfinite(a) || !isfinite(b)) atomicCAS(err, 0, DEV_BAD_AXIS);
+    }
   if (k >= n_out) return;
   const double x0 = x[0], x1 = x[n_raw - 1];
   const double step = __ddiv_rn(__dsub_rn(x1, x0), (double)(n_out - 1));
   // explicit roundings (no FMA contraction) keep the grid and the blend
   // identical to a plain double evaluation of the same formulas
   const double xk = (k == n_out - 1) ? x1 : __dadd_rn(x0, __dmul_rn((double)k, step));
-  // segment s: largest index in [0, n_raw - 2] with x[s] < xk (0 if none)
-  int lo = 0, hi = n_raw - 2;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (x[mid] < xk) lo = mid; else hi = mid - 1;
-  }
-  const int s = lo;
+  const int e = (int)((float)k * ((float)(n_raw - 2) / (float)(n_out - 1)));  // FP32 start
+  const int s = find_segment(x, n_raw, xk, e);
   const double xa = x[s], xb = x[s + 1];
   const double t = __ddiv_rn(__dsub_rn(xk, xa), __dsub_rn(xb, xa));
   const double r = ref ? (double)ref[k] : 0.0;
-  const int j0 = blockIdx.y * INTERP_ROWS;
-  const int j1 = min(m, j0 + INTERP_ROWS);
+  const int j0 = blockIdx.y * rows_per_block;
+  const int j1 = min(m, j0 + rows_per_block);
   for (int j = j0; j < j1; ++j) {
     const double ya = (double)y[(size_t)j * n_raw + s];
     const double yb = (double)y[(size_t)j * n_raw + s + 1];
@@ -261,9 +298,13 @@ cudaError_t launch_interp_t(int m, int n, const double* t, const float* y, long 
 
 cudaError_t launch_interp(int m, int n_raw, const double* x, const float* y, int n_out,
                           float* out, const float* ref, float* dyn, int* err, cudaStream_t s) {
-  k_check_axis<<<(n_raw + 255) / 256, 256, 0, s>>>(n_raw, x, err);
-  dim3 grid((n_out + 127) / 128, (m + INTERP_ROWS - 1) / INTERP_ROWS);
-  k_interp<<<grid, 128, 0, s>>>(m, n_raw, x, y, n_out, out, ref, dyn);
+  // rows per slab: 16, or fewer (down to 4) until the launch has at least two
+  // blocks per SM of a 152-SM GPU (each slab repeats its grid points' search)
+  const int kblocks = (n_out + 127) / 128;
+  int rows = 16;
+  while (rows > 4 && (long)kblocks * ((m + rows - 1) / rows) < 304) rows >>= 1;
+  dim3 grid(kblocks, (m + rows - 1) / rows);
+  k_interp<<<grid, 128, 0, s>>>(m, n_raw, x, y, n_out, rows, out, ref, dyn, err);
   return cudaGetLastError();
 }
 
