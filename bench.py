@@ -725,7 +725,8 @@ def run_ours(args, world, rank, local, pg):
     # so the whole step time stands in for the kernel time
     x_mean = statistics.mean(t["xspec_ms"]) if per_call_timing else ms
     achieved = xbytes / (x_mean / 1e3) / 1e9
-    traffic = xspec_traffic_per_launch(args.workload, args.precision, kernel)
+    # the committed capture is of a whole launch; a rank's part is not that launch
+    traffic = None if strong else xspec_traffic_per_launch(args.workload, args.precision, kernel)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kernel,
                 "grid": (f"{pair_clusters} CTA pairs" if kernel == "k_xspec_pair" else None),
