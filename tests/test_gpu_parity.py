@@ -679,6 +679,46 @@ def test_tile_parts_assemble_the_full_result(ctx, homo):
         ctx.compute_part(d1, d2, 3, 3)
 
 
+@pytest.mark.parametrize("n,m,prec,opts,nparts", [
+    (129, 7, "split", {}, 4),                       # 2 tile rows: more parts than tiles
+    (1000, 33, "bf16", {}, 3),
+    (700, 65, "split", {"no_mirror": True}, 4),
+    (700, 65, "split", {"upper_triangle": True}, 3),
+    (520, 256, "split", {}, 2),
+])
+def test_tile_parts_edge_cases(ctx, n, m, prec, opts, nparts):
+    """Ragged tile edges, BF16, NO_MIRROR (every tile, no mirrored blocks), the upper
+    triangle (no mirrored blocks: nu2 >= nu1 and the diagonal tiles' mirrored lower
+    halves), and more parts than tiles (empty parts write nothing)."""
+    import paper_1808_00685_gb300 as pkg
+    y = workloads.random_stack(m, n, seed=n + m, offset=-1.5)
+    d = dev(y)
+    ophi, opsi, _, _ = oracle.corr2d(y)
+    upper = opts.get("upper_triangle", False)
+    got = []
+    for part in range(nparts):
+        phi, psi, _ = pkg.Context.alloc_out(n, n, d.device)
+        phi.fill_(float("nan"))
+        psi.fill_(float("nan"))
+        ph, ps = ctx.compute_part(d, None, part, nparts, precision=prec, out=(phi, psi), **opts)
+        ctx.synchronize()
+        got.append((host(ph), host(ps)))
+        tiles = pkg.corr2d_plan_part(n, n, True, pkg.FLAG_NO_MIRROR if opts.get("no_mirror") else 0,
+                                     part, nparts)
+        if not tiles:
+            assert np.all(np.isnan(got[-1][0])) and np.all(np.isnan(got[-1][1]))
+    wp = np.stack([~np.isnan(a) for a, _ in got])
+    phi = np.where(wp, np.stack([a for a, _ in got]), 0.0).sum(0)
+    psi = np.where(wp, np.stack([b for _, b in got]), 0.0).sum(0)
+    if upper:
+        iu = np.triu_indices(n)
+        assert np.all(wp.sum(0)[iu] == 1)
+        check(phi[iu], psi[iu], ophi[iu], opsi[iu], TOL[prec], f"upper triangle in {nparts} parts")
+    else:
+        assert np.all(wp.sum(0) == 1)
+        check(phi, psi, ophi, opsi, TOL[prec], f"{nparts} parts {prec} {opts}")
+
+
 def test_upper_triangle_output(ctx):
     """CORR2D_FLAG_UPPER_TRIANGLE: nu2 >= nu1 equals the full result; lower boxes
     away from the diagonal are not written (sentinel NaNs stay)."""
