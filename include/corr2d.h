@@ -30,6 +30,11 @@
  *   the GPU finishes.  Results are valid once the stream has been
  *   synchronised; corr2d_synchronize() does that and also reports device-side
  *   wait time-outs.
+ * - The work of one context must not overlap on the GPU: its calls share the
+ *   context's workspace (operand rows, descriptors) and the cross-spectrum
+ *   kernel's work counters.  Calls on one stream are ordered; before switching
+ *   streams with corr2d_set_stream, let the old stream's work finish (or order
+ *   the streams with an event).  Use one context per concurrent stream.
  * - No function throws or aborts.  Each returns a corr2d_status; on failure
  *   corr2d_last_error() describes the first problem found.  Arguments are
  *   validated before anything is launched, so a rejected call leaves outputs
@@ -118,7 +123,8 @@ corr2d_status corr2d_create(corr2d_ctx** out, int device, void* cuda_stream);
 /* Release a context and its device workspace (synchronises its stream). */
 corr2d_status corr2d_destroy(corr2d_ctx* ctx);
 
-/* Change the stream later calls enqueue on. */
+/* Change the stream later calls enqueue on (the context's earlier work must
+ * not overlap the later calls' on the GPU: see the conventions above). */
 corr2d_status corr2d_set_stream(corr2d_ctx* ctx, void* cuda_stream);
 
 /* Text of the last failure on this context ("" after success). NULL ctx
