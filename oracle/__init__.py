@@ -9,11 +9,14 @@ The arithmetic lives in ``corr2d_oracle.c`` (plain double loops, direct
 O(m^2) DFT, no FFT); this module compiles it with the host C compiler on first
 use and exposes it through ctypes with numpy arrays.  Every function cites the
 passage of the paper it states; the readings taken where the paper is silent
-or inconsistent are listed at the top of the C file (R1..R12).
+or inconsistent are listed at the top of the C file (R1..R13); ``reduce_map`` states its
+own (R14) in its docstring.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (brute force by a second formula, library special cases, Parseval, closed
-forms, invariants and the Noda sign rules).  None is "parity unpinned".
+forms, invariants, the Noda sign rules, and for ``hilbert_noda`` the matrix
+written out by hand, the sawtooth series and FT/HT agreement); the module
+docstring there names the pins of each function.  None is "parity unpinned".
 """
 from __future__ import annotations
 

@@ -11,7 +11,7 @@
  * Everything is plain double arithmetic, straight loops, no blocking, no
  * fusion, no FFT.  Each function names the passage of the paper it follows.
  * Where the paper is silent or inconsistent the reading taken is written next
- * to the code (readings R1..R13, listed again in the design notes):
+ * to the code (readings R1..R13):
  *
  *  R1  Eq. disint2d sums over all m frequencies; for real input that sum is
  *      real (Eq. symmeFT), so the asynchronous part would vanish.  The package
