@@ -469,7 +469,7 @@ class Context:
         return phi[:, :n2], psi[:, :n2]
 
     def compute_part(self, y1, y2, part, nparts, precision="split", alpha=0.0, norm=0.0,
-                     no_mirror=False, upper_triangle=False, out=None):
+                     no_mirror=False, upper_triangle=False, hilbert=False, out=None):
         """Part `part` of `nparts` of the output tiles (and their mirrors) of Phi and Psi,
         written at their places in full n1 x n2 buffers; other elements are untouched."""
         m, n1 = y1.shape
@@ -480,7 +480,7 @@ class Context:
             phi, psi = out
             ldo = phi.stride(0)
         params = make_params(precision, alpha, norm, no_mirror=no_mirror,
-                             upper_triangle=upper_triangle)
+                             upper_triangle=upper_triangle, hilbert=hilbert)
         corr2d_compute_part(self.handle, m, n1, _ptr(y1), y1.stride(0), n2, _ptr(y2),
                             y2.stride(0) if y2 is not None else 0, params, part, nparts,
                             _ptr(phi), _ptr(psi), ldo)

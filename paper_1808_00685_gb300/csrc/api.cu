@@ -518,7 +518,9 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   uint16_t* opA = (uint16_t*)ops;
   uint16_t* opB = (homo && !hilbert) ? opA : (uint16_t*)(ops + pl.bytesA);
   float* s1 = (float*)(ops + pl.off_s1);
-  float* s2 = homo ? s1 : (float*)(ops + pl.off_s2);
+  // the Hilbert variant's two operands come from different matrices, and
+  // each row's scale carries its operand's power-of-two rescale: two scales
+  float* s2 = (homo && !hilbert) ? s1 : (float*)(ops + pl.off_s2);
 
   std::vector<PrepJob> jobs;
   std::vector<PrepItem> pitems;
@@ -540,7 +542,7 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   } else if (homo) {
     // the two operands of the Hilbert variant use different matrices
     mkjob(y1, ld1, n1, r1, opA, nullptr, s1, sig1, wtab);
-    mkjob(y1, ld1, n1, r1, nullptr, opB, s1, nullptr, wtab_b);
+    mkjob(y1, ld1, n1, r1, nullptr, opB, s2, nullptr, wtab_b);
   } else {
     mkjob(y1, ld1, n1, r1, opA, nullptr, s1, sig1, wtab);
     mkjob(y2, ld2, n2, r2, nullptr, opB, s2, sig2, hilbert ? wtab_b : wtab);
@@ -1467,7 +1469,7 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
       uint16_t* opA = (uint16_t*)(ops + offA[i]);
       uint16_t* opB = (homo && !hilbert) ? opA : (uint16_t*)(ops + offB[i]);
       float* sc1 = (float*)(ops + offS1[i]);
-      float* sc2 = homo ? sc1 : (float*)(ops + offS2[i]);
+      float* sc2 = (homo && !hilbert) ? sc1 : (float*)(ops + offS2[i]);
       auto mkjob = [&](const float* y, int n, uint16_t* a, uint16_t* b, float* sc,
                        const uint8_t* table) {
         PrepJob j{};
@@ -1482,7 +1484,7 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
         mkjob(q.y1, q.n1, opA, nullptr, sc1, wtab);  // opB == opA
       } else if (homo) {
         mkjob(q.y1, q.n1, opA, nullptr, sc1, wtab);
-        mkjob(q.y1, q.n1, nullptr, opB, sc1, wtab_b);
+        mkjob(q.y1, q.n1, nullptr, opB, sc2, wtab_b);
       } else {
         mkjob(q.y1, q.n1, opA, nullptr, sc1, wtab);
         mkjob(q.y2, n2, nullptr, opB, sc2, hilbert ? wtab_b : wtab);

@@ -211,7 +211,7 @@ extern "C" corr2d_status corr2d_compute_noalloc(int device, void* cuda_stream, i
   const size_t off_a = off;  off = up(off + (size_t)n1 * rowlen * 2, 1024);
   const size_t off_b = off;  off = up(off + (shared_rows ? 0 : (size_t)n2 * rowlen * 2), 1024);
   const size_t off_s1 = off; off = up(off + (size_t)n1 * 4, 256);
-  const size_t off_s2 = off; off = up(off + (homo ? 0 : (size_t)n2 * 4), 256);
+  const size_t off_s2 = off; off = up(off + (shared_rows ? 0 : (size_t)n2 * 4), 256);
   const size_t off_jobs = off; off = up(off + njobs * sizeof(PrepJob), 128);
   const size_t off_pit = off; off = up(off + npitems * sizeof(PrepItem), 128);
   const size_t off_prob = off; off = up(off + sizeof(XProblem), 128);
@@ -241,7 +241,9 @@ extern "C" corr2d_status corr2d_compute_noalloc(int device, void* cuda_stream, i
   uint16_t* opA = (uint16_t*)(S + off_a);
   uint16_t* opB = shared_rows ? opA : (uint16_t*)(S + off_b);
   float* s1 = (float*)(S + off_s1);
-  float* s2 = homo ? s1 : (float*)(S + off_s2);
+  // each row's scale carries its operand's power-of-two rescale, which differs
+  // between the Hilbert variant's two matrices: a scale array per operand
+  float* s2 = shared_rows ? s1 : (float*)(S + off_s2);
   const float* ref1 = p.ref_mode == CORR2D_REF_USER ? p.ref1 : nullptr;
   const float* ref2 = p.ref_mode == CORR2D_REF_USER ? (homo ? p.ref1 : p.ref2) : nullptr;
   std::vector<PrepJob> jobs(njobs);
@@ -259,7 +261,7 @@ extern "C" corr2d_status corr2d_compute_noalloc(int device, void* cuda_stream, i
     j.ref = from_y2 ? ref2 : ref1;
     j.outA = second ? nullptr : opA;
     j.outB = second ? opB : nullptr;  // job 0 with shared rows: opB == opA
-    j.scale = from_y2 ? s2 : s1;      // a homo Hilbert problem writes s1 twice, same values
+    j.scale = second ? s2 : s1;
     j.sigma_out = nullptr;
     j.wtab = S + ((second && hilbert) ? off_tw2 : off_tw);
     j.m = m;

@@ -81,3 +81,20 @@ def test_c5_fixed_n_keeps_the_m_mix():
     assert [p.homo for p in full.problems] == [p.homo for p in small.problems]
     assert all(p.n1 == p.n2 == 768 for p in small.problems)
     assert small.total_outputs == 512 * 768 * 768
+
+
+def test_step_stack_puts_the_hilbert_transform_in_a_higher_binade():
+    """The step-response stack exists to make the Hilbert variant's two operands
+    (the dynamic spectrum d and its transform N d, Eq. HilbNoda) have their largest
+    entries in different powers of two for most variables; the oracle's
+    Hilbert-Noda product with the identity as stack 1 gives N d / (m - 1)."""
+    import oracle
+    m, n = 124, 300
+    y = workloads.step_stack(m, n, seed=7)
+    assert y.dtype == np.float32 and np.array_equal(y, workloads.step_stack(m, n, seed=7))
+    d = oracle.dynamic(y, oracle.reference_mean(y))
+    _, nd = oracle.hilbert_noda(np.eye(m), d)
+    nd *= m - 1
+    e_d = np.frexp(np.abs(d).max(axis=0))[1]
+    e_nd = np.frexp(np.abs(nd).max(axis=0))[1]
+    assert (e_nd > e_d).mean() > 0.9

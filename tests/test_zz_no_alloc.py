@@ -66,6 +66,8 @@ def _oracle_ht(y1, y2, alpha):
 def _stacks(case):
     if case == "homo":
         return workloads.sigmoid_bands(64, 1000, 20, seed=21), None
+    if case == "step":  # N d a power of two above d: the two operands rescale differently
+        return workloads.step_stack(124, 519, seed=41), None
     return (workloads.random_stack(100, 700, seed=22, offset=2.0),
             workloads.random_stack(100, 500, seed=23, offset=-1.0))
 
@@ -81,6 +83,7 @@ CASES = [
     ("homo", "split", {"no_mirror": True}),
     ("homo", "split", {"hilbert": True}),
     ("hetero", "split", {"hilbert": True}),
+    ("step", "split", {"hilbert": True}),
 ]
 
 

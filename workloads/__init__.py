@@ -44,6 +44,19 @@ def random_stack(m: int, n: int, seed: int, offset: float = 0.0, scale: float = 
     return (offset + scale * rng.standard_normal((m, n))).astype(np.float32)
 
 
+def step_stack(m: int, n: int, seed: int, offset: float = 1.0, noise: float = 1e-3) -> np.ndarray:
+    """Every variable jumps once, at a step between m/4 and 3m/4, by a random
+    amplitude, plus a little noise.  The discrete Hilbert transform of such a
+    step grows like (2/pi) ln m near the jump, so it is larger than the
+    dynamic spectrum itself for most variables once m is a few dozen."""
+    rng = np.random.default_rng(seed)
+    t = np.arange(m)[:, None]
+    t0 = rng.integers(m // 4, max(m // 4 + 1, 3 * m // 4), size=n)[None, :]
+    amp = rng.uniform(0.5, 2.0, size=n)[None, :] * rng.choice([-1.0, 1.0], size=n)[None, :]
+    y = offset + amp * (t >= t0) + noise * rng.standard_normal((m, n))
+    return y.astype(np.float32)
+
+
 def sinusoid_bands(m: int, n: int, phases_deg, seed: int, noise: float = 0.0,
                    centers=None, widths=None, amps=None, one_period: bool = True):
     """Lorentzian bands with amplitudes a_b sin(2 pi t_j + phi_b), t_j = j/m.
