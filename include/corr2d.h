@@ -221,9 +221,14 @@ corr2d_status corr2d_interpolate_perturbation(corr2d_ctx* ctx, int method, int m
  * mirror 0/1, group 0 for row-major or G for G x G super-blocks, chunk >= 1
  * list entries per CTA at a time; seg > 0 runs the kernel that keeps the
  * stack-1 operand in TMEM, on row segments of seg 128 x 128 tiles, when the
- * problem has at most 8 frequency chunks).  Repeated calls with the same buffers and
- * arguments (up to four recent sets) launch from descriptors already on the
- * device.  The launches use the context's workspace, which a later call with
+ * problem has at most 8 frequency chunks).  The two launches of a call with at
+ * most 4 GiB of output are programmatically dependent: the cross-spectrum
+ * launch's setup overlaps the DFT launch's tail, and it reads the operand
+ * rows only after the DFT launch has completed (CORR2D_PDL=off or =always
+ * overrides the size rule; timing events recorded between the two launches,
+ * see corr2d_set_profiling, serialise them).  Repeated calls with the same
+ * buffers and arguments (up to four recent sets) launch from descriptors
+ * already on the device.  The launches use the context's workspace, which a later call with
  * other shapes may reallocate: do not capture corr2d_compute into a CUDA
  * graph that outlives such calls.  To replay one problem with the least host
  * work, pass it to corr2d_batch as a batch of one: the batch records its own

@@ -62,6 +62,8 @@ struct LaunchPlan {
   bool ta = false;    // cross-spectrum with the stack-1 operand in TMEM (XSeg list)
   int chunk = 1;      // run length of list entries per CTA
   int stages = 4;     // operand stages of the single-CTA kernel
+  bool pdl = false;   // cross-spectrum launch programmatically dependent on the DFT launch
+  XProblem p0{};      // host copy of the one problem (a kernel parameter of the launch)
 };
 
 // A recently used corr2d_compute launch: its key, descriptor offsets and the
@@ -75,10 +77,24 @@ struct PlanSlot {
 };
 constexpr int kPlanSlots = 4;
 
+// The batch's graph executables: the batched DFT launch, the persistent
+// cross-spectrum launch, and both in one graph with the cross-spectrum launch
+// programmatically dependent on the DFT launch (its setup overlaps the DFT's
+// tail).  The timing events sit between the first two on the stream (events
+// recorded inside a graph cannot be waited on or timed from outside it); the
+// third runs when no timings are recorded.
+struct BatchExecs {
+  cudaGraphExec_t prep = nullptr, xspec = nullptr, both = nullptr;
+  bool ready() const { return prep && xspec && both; }
+  void destroy() {
+    for (cudaGraphExec_t* g : {&prep, &xspec, &both})
+      if (*g) { cudaGraphExecDestroy(*g); *g = nullptr; }
+  }
+};
+
 struct BatchCache {
   std::vector<uint8_t> key;   // serialized problem list + params
-  cudaGraphExec_t exec = nullptr;     // batched DFT launch
-  cudaGraphExec_t exec_x = nullptr;   // persistent cross-spectrum launch
+  BatchExecs ex;
   DevBuf desc;                // device descriptors of this batch
   DevBuf ops;                 // operand rows + scales
   std::vector<int> bn;        // chosen tile width per problem
@@ -108,6 +124,7 @@ struct corr2d_ctx {
   DevBuf spline;    // perturbation-axis spline: knot tables + second derivatives
   bool fault_alloc = false;
   int fault_inject = 0;  // CORR2D_FAULT=stall: the cross-spectrum producer never arrives
+  int pdl_mode = 1;      // CORR2D_PDL: 0 off, 1 by output size (default), 2 always
   bool profiling = false;
   bool recorded = false;
   int last_xspec = CORR2D_XSPEC_NONE;  // kernel of the last compute / batch call
@@ -406,6 +423,10 @@ corr2d_status upload_blob(corr2d_ctx* ctx, DevBuf& dev, std::vector<uint8_t>& la
   return CORR2D_OK;
 }
 
+bool use_pdl(const corr2d_ctx* ctx, double out_bytes) {
+  return ctx->pdl_mode == 2 || (ctx->pdl_mode == 1 && out_bytes <= kPdlMaxOutBytes);
+}
+
 struct TcPlan {
   int planes, kp, nch, rowlen;
   size_t bytesA, bytesB, off_s1, off_s2, total;
@@ -476,7 +497,8 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
       CUDA_TRY(ctx, launch_xspec_tc((const XProblem*)(d + lp.off_probs),
                                     (const XItem*)(d + lp.off_xitems), lp.nxitems, lp.planes,
                                     ctx->sm_count, ctx->d_err, ctx->limit_ns, ctx->stream,
-                                    ctx->fault_inject, lp.chunk, lp.stages));
+                                    ctx->fault_inject, lp.chunk, lp.stages, 1,
+                                    !lp.skip_prep && lp.pdl, &lp.p0));
     if (ctx->profiling) {
       cudaEventRecord(ctx->ev[2], ctx->stream);
       ctx->recorded = true;
@@ -604,6 +626,8 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   lp.ta = ta;
   lp.chunk = (pair || ta) ? 1 : std::max(1, tc.chunk);
   lp.stages = tc.stages == 5 ? 5 : 4;
+  lp.pdl = use_pdl(ctx, (double)out_rows * (double)n2 * 8.0);
+  lp.p0 = xp;
   if (slot) {
     slot->plan = lp;
     slot->plan.key = key;
@@ -781,6 +805,8 @@ corr2d_status corr2d_create(corr2d_ctx** out, int device, void* cuda_stream) {
     long v = atol(lim);
     if (v > 0) ctx->limit_ns = (unsigned long long)v * 1000000ull;
   }
+  if (const char* pm = getenv("CORR2D_PDL"))
+    ctx->pdl_mode = strcmp(pm, "off") == 0 ? 0 : strcmp(pm, "always") == 0 ? 2 : 1;
   if (const char* f = getenv("CORR2D_FAULT")) {
     ctx->fault_alloc = (strcmp(f, "alloc") == 0);
     ctx->fault_inject = (strcmp(f, "stall") == 0) ? 1 : 0;
@@ -801,8 +827,7 @@ corr2d_status corr2d_destroy(corr2d_ctx* ctx) {
   release(ctx->spline);
   release(ctx->batch.desc);
   release(ctx->batch.ops);
-  if (ctx->batch.exec) cudaGraphExecDestroy(ctx->batch.exec);
-  if (ctx->batch.exec_x) cudaGraphExecDestroy(ctx->batch.exec_x);
+  ctx->batch.ex.destroy();
   for (auto& kv : ctx->twiddles) release(kv.second);
   for (auto& kv : ctx->simt_tw) release(kv.second);
   if (ctx->d_err) cudaFree(ctx->d_err);
@@ -1398,7 +1423,7 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
   // A problem list and parameters identical to the ones the cached graph was
   // recorded for were validated then; the replay skips the per-pointer
   // attribute queries (two thousand driver calls for 512 problems).
-  const bool same = bc.exec && bc.exec_x && bc.key == key;
+  const bool same = bc.ex.ready() && bc.key == key;
   if (!same) {
     for (int i = 0; i < count; ++i) {
       const corr2d_problem& q = hp[i];
@@ -1407,20 +1432,18 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
       if (st != CORR2D_OK) return fail(ctx, st, "problem %d: %s", i, ctx->err.c_str());
     }
   }
-  // The two launches are captured as two graph executables; the timing events
-  // sit between them on the stream (events recorded inside a graph cannot be
-  // waited on or timed from outside it).
-  auto replay = [&](cudaGraphExec_t gp, cudaGraphExec_t gx) -> cudaError_t {
-    if (ctx->profiling) cudaEventRecord(ctx->ev[0], ctx->stream);
-    cudaError_t e = cudaGraphLaunch(gp, ctx->stream);
-    if (ctx->profiling) cudaEventRecord(ctx->ev[1], ctx->stream);
-    if (e == cudaSuccess) e = cudaGraphLaunch(gx, ctx->stream);
-    if (ctx->profiling) cudaEventRecord(ctx->ev[2], ctx->stream);
+  auto replay = [&](const BatchExecs& x) -> cudaError_t {
+    if (!ctx->profiling) return cudaGraphLaunch(x.both, ctx->stream);
+    cudaEventRecord(ctx->ev[0], ctx->stream);
+    cudaError_t e = cudaGraphLaunch(x.prep, ctx->stream);
+    cudaEventRecord(ctx->ev[1], ctx->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(x.xspec, ctx->stream);
+    cudaEventRecord(ctx->ev[2], ctx->stream);
     return e;
   };
   if (same) {
     ctx->last_xspec = CORR2D_XSPEC_TC;
-    CUDA_TRY(ctx, replay(bc.exec, bc.exec_x));
+    CUDA_TRY(ctx, replay(bc.ex));
     ctx->recorded = ctx->profiling;
     ctx->err.clear();
     return CORR2D_OK;
@@ -1519,8 +1542,8 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
                    (probs[i].n1 + TILE_M - 1) / TILE_M, probs[i].mirror ? group : 0);
     return CORR2D_OK;
   };
-  auto make_graph = [&](int bn_threshold, int chunk, int full_kp, int group,
-                        cudaGraphExec_t* exec, cudaGraphExec_t* exec_x) -> corr2d_status {
+  auto make_graph = [&](int bn_threshold, int chunk, int full_kp, int group, BatchExecs* out)
+      -> corr2d_status {
     std::vector<PrepJob> jobs;
     std::vector<PrepItem> pitems;
     std::vector<XProblem> probs;
@@ -1528,45 +1551,46 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
     corr2d_status s2 = build(bn_threshold, full_kp, group, jobs, pitems, probs, xitems);
     if (s2 != CORR2D_OK) return s2;
     Blob b = pack(jobs, pitems, probs, xitems);
-    std::vector<uint8_t> last;
     if ((s2 = ensure(ctx, bc.desc, b.bytes.size())) != CORR2D_OK) return s2;
     CUDA_TRY(ctx, cudaMemcpyAsync(bc.desc.p, b.bytes.data(), b.bytes.size(), cudaMemcpyHostToDevice, ctx->stream));
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     uint8_t* d = (uint8_t*)bc.desc.p;
+    auto prep = [&](cudaStream_t cs) {
+      return launch_prep_tc((const PrepJob*)(d + b.off_jobs), (const PrepItem*)(d + b.off_pitems),
+                            b.npitems, planes, max_kp, ctx->d_err, ctx->limit_ns, cs);
+    };
+    auto xspec = [&](cudaStream_t cs, bool pdl) {
+      return launch_xspec_tc((const XProblem*)(d + b.off_probs), (const XItem*)(d + b.off_xitems),
+                             b.nxitems, planes, ctx->sm_count, ctx->d_err, ctx->limit_ns, cs, 0,
+                             chunk, 4, count, pdl, count == 1 ? probs.data() : nullptr);
+    };
+    // three captures: the DFT launch, the cross-spectrum launch, and both with
+    // the cross-spectrum launch programmatically dependent on the DFT launch
     cudaStream_t cs;
     CUDA_TRY(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t graph = nullptr, graph_x = nullptr;
-    CUDA_TRY(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e1 = launch_prep_tc((const PrepJob*)(d + b.off_jobs), (const PrepItem*)(d + b.off_pitems),
-                                    b.npitems, planes, max_kp, ctx->d_err, ctx->limit_ns, cs);
-    cudaError_t e3 = cudaStreamEndCapture(cs, &graph);
-    cudaError_t e2 = cudaSuccess, e5 = cudaSuccess;
-    if (e1 == cudaSuccess && e3 == cudaSuccess) {
-      e5 = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-      if (e5 == cudaSuccess) {
-        e2 = launch_xspec_tc((const XProblem*)(d + b.off_probs), (const XItem*)(d + b.off_xitems),
-                             b.nxitems, planes, ctx->sm_count, ctx->d_err, ctx->limit_ns, cs, 0,
-                             chunk);
-        e5 = cudaStreamEndCapture(cs, &graph_x);
-      }
+    cudaGraph_t g[3] = {nullptr, nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) break;
+      cudaError_t el = cudaSuccess;
+      if (k != 1) el = prep(cs);
+      if (k != 0 && el == cudaSuccess) el = xspec(cs, k == 2 && ctx->pdl_mode != 0);
+      e = cudaStreamEndCapture(cs, &g[k]);
+      if (e == cudaSuccess) e = el;
     }
     cudaStreamDestroy(cs);
-    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e5 != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      if (graph_x) cudaGraphDestroy(graph_x);
-      return fail(ctx, CORR2D_ECUDA, "batch graph capture failed: %s / %s / %s / %s",
-                  cudaGetErrorString(e1), cudaGetErrorString(e2), cudaGetErrorString(e3),
-                  cudaGetErrorString(e5));
+    cudaGraphExec_t* dst[3] = {&out->prep, &out->xspec, &out->both};
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaGraphInstantiate(dst[k], g[k], 0);
+    for (int k = 0; k < 3; ++k)
+      if (g[k]) cudaGraphDestroy(g[k]);
+    if (e != cudaSuccess) {
+      out->destroy();
+      return fail(ctx, CORR2D_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
     }
-    cudaError_t e4 = cudaGraphInstantiate(exec, graph, 0);
-    if (e4 == cudaSuccess) e4 = cudaGraphInstantiate(exec_x, graph_x, 0);
-    cudaGraphDestroy(graph);
-    cudaGraphDestroy(graph_x);
-    if (e4 != cudaSuccess) return fail(ctx, CORR2D_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e4));
     return CORR2D_OK;
   };
-  if (bc.exec) { cudaGraphExecDestroy(bc.exec); bc.exec = nullptr; }
-  if (bc.exec_x) { cudaGraphExecDestroy(bc.exec_x); bc.exec_x = nullptr; }
+  bc.ex.destroy();
   // tuner: time the batch graph for each candidate, keep the fastest:
   // tile width (bn = 64 below a problem size) x run length per CTA x the
   // frequency count up to which homo problems use full tiles
@@ -1585,8 +1609,8 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
       const int thr = thresholds[cand % 3], chunk = chunks[(cand / 3) % 2];
       const int group = groups[(cand / 6) % 2];
       const int full_kp = full_kps[cand / 12];
-      cudaGraphExec_t ex = nullptr, exx = nullptr;
-      if ((st = make_graph(thr, chunk, full_kp, group, &ex, &exx)) != CORR2D_OK) {
+      BatchExecs ex;
+      if ((st = make_graph(thr, chunk, full_kp, group, &ex)) != CORR2D_OK) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         return st;
@@ -1594,16 +1618,14 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
       float ms = 1e30f;
       for (int rep = 0; rep < 3; ++rep) {  // a warm-up, then the faster of two
         cudaEventRecord(e0, ctx->stream);
-        cudaGraphLaunch(ex, ctx->stream);
-        cudaGraphLaunch(exx, ctx->stream);
+        cudaGraphLaunch(ex.both, ctx->stream);
         cudaEventRecord(e1, ctx->stream);
         cudaEventSynchronize(e1);
         float t = 0.f;
         cudaEventElapsedTime(&t, e0, e1);
         if (rep > 0) ms = std::min(ms, t);
       }
-      cudaGraphExecDestroy(ex);
-      cudaGraphExecDestroy(exx);
+      ex.destroy();
       if (getenv("CORR2D_VERBOSE"))
         fprintf(stderr, "corr2d batch tuner: bn=64 below n=%d, runs of %d, full tiles up to %d "
                 "frequencies, mirrored order %d -> %.4f ms\n", thr, chunk, full_kp, group, ms);
@@ -1618,12 +1640,11 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
-  if ((st = make_graph(best_thr, best_chunk, best_full, best_group, &bc.exec, &bc.exec_x)) !=
-      CORR2D_OK)
+  if ((st = make_graph(best_thr, best_chunk, best_full, best_group, &bc.ex)) != CORR2D_OK)
     return st;
   bc.key = key;
   ctx->last_xspec = CORR2D_XSPEC_TC;
-  CUDA_TRY(ctx, replay(bc.exec, bc.exec_x));
+  CUDA_TRY(ctx, replay(bc.ex));
   ctx->recorded = ctx->profiling;
   ctx->err.clear();
   return CORR2D_OK;

@@ -125,9 +125,24 @@ cudaError_t launch_prep_tc(const PrepJob* d_jobs, const PrepItem* d_items, int n
 // inject & 1 makes the producer issue nothing (host-requested fault for the
 // time-out test); 0 in normal operation.  Each CTA takes runs of `chunk`
 // consecutive work items; `stages` (4 or 5) operand stages are in flight.
+// Programmatic dependent launch of the cross-spectrum kernel behind the DFT
+// kernel: its launch latency and setup then overlap the DFT's tail.  Measured
+// on GB300 per call without per-launch events (which serialise the two):
+// homo m = 64 n = 4096 42.0-42.6 -> 39.9-41.0 us, hetero m = 128 8192 x 2048
+// 48.5-49.8 -> 45.1 us, homo m = 256 n = 8192 125.9 -> 122.5-122.9 us,
+// n = 16384 374.7-375.6 -> 371.5-372.7 us, but n = 32768 (8.6 GB of output)
+// 1.39-1.45 -> 1.42-1.53 ms, that long launch running at lower SM clocks.  By
+// default it is used up to this much output.
+constexpr double kPdlMaxOutBytes = 4.0 * 1024.0 * 1024.0 * 1024.0;
+
 cudaError_t launch_xspec_tc(const XProblem* d_probs, const XItem* d_items, int nitems,
                             int planes, int grid, int* err, unsigned long long limit_ns,
-                            cudaStream_t s, int inject = 0, int chunk = 1, int stages = 4);
+                            cudaStream_t s, int inject = 0, int chunk = 1, int stages = 4,
+                            int nprobs = 0, bool pdl = false, const XProblem* h_p0 = nullptr);
+// nprobs: problems in the list (0: unknown); with nprobs == 1, h_p0 is a host
+// copy of d_probs[0], passed as a kernel parameter.  pdl: launch with
+// programmatic stream serialization, only when the DFT kernel is the launch
+// just ahead of it in the stream (its setup then overlaps the DFT's tail).
 
 // Row segment of the TMEM-operand cross-spectrum kernel: tiles (ti, tj0 ..
 // tj0 + ntj - 1) of 128 x 128 outputs that share their stack-1 rows.

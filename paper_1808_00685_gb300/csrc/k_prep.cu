@@ -210,6 +210,9 @@ __global__ void __launch_bounds__(PREP_THREADS, 2) k_prep_tc(const PrepJob* __re
                                                           int* err, unsigned long long limit_ns) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // The cross-spectrum launch behind this one may start its setup on free SMs
+  // now; it waits for this launch to complete before it reads anything.
+  griddep_launch_dependents();
   const PrepItem item = items[blockIdx.x];
   const PrepJob& job = jobs[item.job];
   const int m = job.m, n = job.n, kp = job.kp;

@@ -115,8 +115,9 @@ __device__ __forceinline__ XItem read_sched(const XItem* p) {
 
 template <int P>
 __global__ void __launch_bounds__(XS_THREADS, 1)
-    k_xspec_tc(const XProblem* __restrict__ probs, const XItem* __restrict__ items, int nitems,
-               int* err, unsigned long long limit_ns, int inject, int chunk, int nst) {
+    k_xspec_tc(const XProblem* __restrict__ plist, const XItem* __restrict__ items, int nitems,
+               int* err, unsigned long long limit_ns, int inject, int chunk, int nst,
+               int nprobs, const __grid_constant__ XProblem p0) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* stages = base;
@@ -127,6 +128,12 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
   uint32_t* tmem_slot = (uint32_t*)(bars + XS_NBARS);
   XItem* sched = (XItem*)(tmem_slot + 2);  // schedule ring (8-byte aligned)
   XItem* first_sm = sched + XS_SCHED;      // this CTA's first tile
+  // A launch with one problem takes it (tensor maps included) from the kernel
+  // parameters, which arrive with the launch; the descriptor list in global
+  // memory may have been evicted from L2, and the first TMA copies would wait
+  // for its DRAM reads.
+  const bool one = nprobs == 1;
+  const XProblem* probs = one ? &p0 : plist;
   auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
   auto empty_bar = [&](int s) { return smem_u32(&bars[XS_STAGES + s]); };
   auto tfull_bar = [&](int b) { return smem_u32(&bars[2 * XS_STAGES + b]); };
@@ -145,10 +152,20 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
     XItem f{-1, 0, 0};
     if (first_it < nitems) {
       f = items[first_it];
-      tma_prefetch_desc(&probs[f.prob].tmA);
-      tma_prefetch_desc(&probs[f.prob].tmB);
+      if (!one) {
+        tma_prefetch_desc(&probs[f.prob].tmA);
+        tma_prefetch_desc(&probs[f.prob].tmB);
+        tma_prefetch_desc(&probs[f.prob].tmPhi);
+        tma_prefetch_desc(&probs[f.prob].tmPsi);
+      }
     }
     *first_sm = f;
+  }
+  if (threadIdx.x == 96 && one) {  // in parallel with the list read above
+    tma_prefetch_desc(&probs[0].tmA);
+    tma_prefetch_desc(&probs[0].tmB);
+    tma_prefetch_desc(&probs[0].tmPhi);
+    tma_prefetch_desc(&probs[0].tmPsi);
   }
   if (threadIdx.x == 0) {
     for (int s = 0; s < XS_STAGES; ++s) {
@@ -173,6 +190,10 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // Launched behind the DFT kernel with programmatic serialization, the setup
+  // above overlaps its tail; operand rows, scales and the work counter are
+  // touched only after it has completed.
+  griddep_wait();
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -215,16 +236,6 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
           nch = pr->nchunks;
           bn = pr->bn;
         }
-        {  // warm the TMA unit's descriptor cache for the next problem
-          const int nx = (pos < chunk && it + 1 < nitems) ? it + 1 : ahead;
-          if (nx < nitems) {
-            const int np = items[nx].prob;
-            if (np != w.prob) {
-              tma_prefetch_desc(&probs[np].tmA);
-              tma_prefetch_desc(&probs[np].tmB);
-            }
-          }
-        }
         for (int c = 0; c < nch; ++c) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, wc)) { ok = false; break; }
           mbar_arrive_expect_tx(full_bar(stage), (uint32_t)(TILE_M + bn) * 128u);
@@ -235,6 +246,20 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
           tma_load_2d_hint(sa, &pr->tmA, cx, (int)w.ti * TILE_M, full_bar(stage), keep);
           tma_load_2d_hint(sa + TILE_M * 128, &pr->tmB, cx, (int)w.tj * bn, full_bar(stage), keep);
           if (++stage == nst) { stage = 0; phase ^= 1u; }
+        }
+        // Warm the TMA unit's descriptor cache for the next problem.  This
+        // comes after the tile's loads: at the first tile the next run is the
+        // result of the work-counter atomic, and waiting for it (and for the
+        // list entry it names) before the first loads delayed them ~1.5 us.
+        if (ok) {
+          const int nx = (pos < chunk && it + 1 < nitems) ? it + 1 : ahead;
+          if (nx < nitems) {
+            const int np = items[nx].prob;
+            if (np != w.prob) {
+              tma_prefetch_desc(&probs[np].tmA);
+              tma_prefetch_desc(&probs[np].tmB);
+            }
+          }
         }
       }
       // every load this thread started has landed before shared memory is released
@@ -462,18 +487,31 @@ cudaError_t init_xspec_kernels() {
 
 cudaError_t launch_xspec_tc(const XProblem* d_probs, const XItem* d_items, int nitems, int planes,
                             int grid, int* err, unsigned long long limit_ns, cudaStream_t s,
-                            int inject, int chunk, int stages) {
+                            int inject, int chunk, int stages, int nprobs, bool pdl,
+                            const XProblem* h_p0) {
+  static const XProblem kNone{};
   if (nitems <= 0) return cudaSuccess;
   if (chunk < 1) chunk = 1;
   if (stages != XS_STAGES) stages = 4;
   if ((long)grid * chunk > nitems) grid = (nitems + chunk - 1) / chunk;
+  // a one-problem launch needs the problem itself as a parameter
+  if (nprobs == 1 && !h_p0) nprobs = 0;
+  const XProblem* p0 = (nprobs == 1) ? h_p0 : &kNone;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(XS_THREADS);
+  cfg.dynamicSmemBytes = XS_SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
   if (planes == 2)
-    k_xspec_tc<2><<<grid, XS_THREADS, XS_SMEM, s>>>(d_probs, d_items, nitems, err, limit_ns, inject,
-                                                    chunk, stages);
-  else
-    k_xspec_tc<1><<<grid, XS_THREADS, XS_SMEM, s>>>(d_probs, d_items, nitems, err, limit_ns, inject,
-                                                    chunk, stages);
-  return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, k_xspec_tc<2>, d_probs, d_items, nitems, err, limit_ns, inject,
+                              chunk, stages, nprobs, *p0);
+  return cudaLaunchKernelEx(&cfg, k_xspec_tc<1>, d_probs, d_items, nitems, err, limit_ns, inject,
+                            chunk, stages, nprobs, *p0);
 }
 
 }  // namespace c2d

@@ -322,7 +322,8 @@ extern "C" corr2d_status corr2d_compute_noalloc(int device, void* cuda_stream, i
                        (int)pit.size(), planes, kp, err, limit_ns, stream);
   if (e == cudaSuccess)
     e = launch_xspec_tc((const XProblem*)(S + off_prob), (const XItem*)(S + off_xit),
-                        (int)items.size(), planes, ds->sm_count, err, limit_ns, stream);
+                        (int)items.size(), planes, ds->sm_count, err, limit_ns, stream, 0, 1, 4,
+                        1, 8.0 * n1 * n2 <= kPdlMaxOutBytes, &xp);
   // The host-side descriptors above must outlive the copies: wait for the stream.
   cudaError_t es = cudaStreamSynchronize(stream);
   if (e != cudaSuccess || es != cudaSuccess)

@@ -179,6 +179,19 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// ------------------------------------------------ programmatic dependent launch
+// A kernel launched with programmatic stream serialization may start before
+// the kernel ahead of it in the stream has finished, once every CTA of that
+// kernel has executed launch_dependents (or exited).  griddep_wait blocks until
+// the kernel ahead has completed and its memory is visible; in a kernel
+// launched without the attribute it returns at once.
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // -------------------------------------------------------------------- tcgen05
 // TMEM allocation: one full warp executes these.
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
