@@ -372,42 +372,56 @@ def timed_steps(ctx, stream, step, flush, steps, warmup, per_call_timing=True):
     bracketed by CUDA events on the stream the library launches on.  The timed steps
     carry no per-launch events: an event between the DFT and cross-spectrum launches
     costs several microseconds per step and serialises the two (the cross-spectrum
-    launch would otherwise overlap the DFT's tail).  With `per_call_timing`, a second
-    pass of the same steps (one warm-up) records the library's per-launch events and
-    gives the prep and cross-spectrum kernel times.  Returns per-step times (ms) of the
-    timed region, the kernel times and the second pass's step times."""
+    launch would otherwise overlap the DFT's tail).  With `per_call_timing`, every
+    timed step is followed by one more step of the same work, outside the timed
+    events, in which the library records events around its two launches; those give
+    the prep and cross-spectrum kernel times under the same clocks and power state as
+    the timed steps beside them.  Returns the timed steps' times (ms), the kernel
+    times and the profiled steps' times."""
     import torch
 
-    def run(k, profile):
-        ctx.set_profiling(profile)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(k)]
-        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        r0.record(stream)
-        prep_ms, xspec_ms = [], []
-        for i in range(k):
-            flush()  # outside the step's events
-            ev[i][0].record(stream)
-            step()
-            ev[i][1].record(stream)
-            if profile:
-                p_ms, x_ms = ctx.timings()  # waits for this step's kernel events
-                prep_ms.append(p_ms)
-                xspec_ms.append(x_ms)
-        r1.record(stream)
-        torch.cuda.synchronize()
-        ctx.synchronize()  # raises on a device-side time-out
-        return [a.elapsed_time(b) for a, b in ev], prep_ms, xspec_ms, r0.elapsed_time(r1)
+    def timed_step():
+        flush()  # outside the step's events
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        return a, b
 
-    run(max(warmup, 0), False)
-    step_ms, _, _, region_ms = run(steps, False)
-    prep_ms, xspec_ms, kstep_ms = [], [], []
-    if per_call_timing:
-        run(1, True)
-        kstep_ms, prep_ms, xspec_ms, _ = run(steps, True)
+    def profiled_step():
+        ctx.set_profiling(True)
+        flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        p_ms, x_ms = ctx.timings()  # waits for this step's kernel events
+        ctx.set_profiling(False)
+        return a, b, p_ms, x_ms
+
     ctx.set_profiling(False)
-    return dict(step_ms=step_ms, prep_ms=prep_ms, xspec_ms=xspec_ms, region_ms=region_ms,
-                profiled_step_ms=kstep_ms)
+    for _ in range(max(warmup, 0)):
+        timed_step()
+        if per_call_timing:
+            profiled_step()
+    torch.cuda.synchronize()
+    ctx.synchronize()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    ev, pev, prep_ms, xspec_ms = [], [], [], []
+    for _ in range(steps):
+        ev.append(timed_step())
+        if per_call_timing:
+            a, b, p_ms, x_ms = profiled_step()
+            pev.append((a, b))
+            prep_ms.append(p_ms)
+            xspec_ms.append(x_ms)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    ctx.synchronize()  # raises on a device-side time-out
+    return dict(step_ms=[a.elapsed_time(b) for a, b in ev], prep_ms=prep_ms, xspec_ms=xspec_ms,
+                region_ms=r0.elapsed_time(r1),
+                profiled_step_ms=[a.elapsed_time(b) for a, b in pev])
 
 
 def sample_block(n, upper=False):
@@ -738,8 +752,9 @@ def run_ours(args, world, rank, local, pg):
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": xbytes,
                 "kernel_ms": round(x_mean, 4),
                 "prep_ms": round(statistics.mean(t["prep_ms"]), 4) if t["prep_ms"] else None,
-                "kernel_timing": ("per-launch CUDA events in a second pass of the same steps "
-                                  "after the timed region" if per_call_timing else
+                "kernel_timing": ("per-launch CUDA events in a profiled step of the same "
+                                  "work after each timed step, outside its events"
+                                  if per_call_timing else
                                   "whole step (several launches per step)"),
                 "profiled_ms_per_step": (round(statistics.mean(t["profiled_step_ms"]), 4)
                                          if t["profiled_step_ms"] else None)}
