@@ -530,8 +530,8 @@ def cpu_baseline_leg(args, y, alpha, checks):
 # ---------------------------------------------------------------- forms
 def run_forms(args, ctx, stream, flush, y, yd, phi, psi, ldo, rows, cols, checks):
     """Comparison forms of the metric on the same inputs, flush and timing: c4 in FP32,
-    BF16 and upper-triangle output; the batch of 512 problems batched, per problem
-    and per problem in FP32.  Sampled GPU outputs go into `checks`."""
+    with BF16 operands, upper-triangle output and BF16 output; the batch of 512 problems
+    batched, per problem and per problem in FP32.  Sampled GPU outputs go into `checks`."""
     import torch
     import paper_1808_00685_gb300 as pkg
     import workloads as wl
@@ -540,16 +540,19 @@ def run_forms(args, ctx, stream, flush, y, yd, phi, psi, ldo, rows, cols, checks
     peak_fp32 = ctx.fp32_peak_tflops()
     peak, _ = measured_peaks()
 
-    def c4_form(name, **kw):
+    def c4_form(name, out=None, **kw):
+        o = out or (phi, psi)
+
         def step():
-            ctx.compute(yd, out=(phi, psi), **kw)
+            ctx.compute(yd, out=o, **kw)
         t = timed_steps(ctx, stream, step, flush, args.steps, args.warmup)
         ms = statistics.mean(t["step_ms"])
         xms = statistics.mean(t["xspec_ms"])
         upper = kw.get("upper_triangle", False)
         outs = n * (n + 1) / 2 if upper else n * n
         d = {"workload": f"homo m={m} n={n} {kw.get('precision', 'split')}"
-                         + (" upper triangle" if upper else ""),
+                         + (" upper triangle" if upper else "")
+                         + (" BF16 output" if kw.get("output_bf16") else ""),
              "ms_per_step": round(ms, 4), "value": n * n / (ms / 1e3),
              "kernel_ms": round(xms, 4), "prep_ms": round(statistics.mean(t["prep_ms"]), 4),
              "steps": args.steps}
@@ -561,18 +564,22 @@ def run_forms(args, ctx, stream, flush, y, yd, phi, psi, ldo, rows, cols, checks
                              "unit": "TFLOP/s", "frac": round(ach / peak_fp32, 4),
                              "peak_kind": "measured: FP32 FMA probe kernel (corr2d_measure_fp32_peak)"}
         else:
-            xb = 8.0 * outs + 1.0 * n * rowlen_elems(m, prec) * 2
+            xb = (4.0 if kw.get("output_bf16") else 8.0) * outs + 1.0 * n * rowlen_elems(m, prec) * 2
             ach = xb / (xms / 1e3) / 1e9
             d["roofline"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak,
                              "unit": "GB/s", "frac": round(ach / peak, 4),
                              "algorithmic_bytes_per_launch": xb}
         r, c = sample_block(n, upper)
-        checks[name] = [(y, None, r, c, 0.0, gather(phi, psi, r, c))]
+        checks[name] = [(y, None, r, c, 0.0, gather(o[0], o[1], r, c))]
         return d
 
     forms["fp32"] = c4_form("fp32", precision="fp32")
     forms["bf16"] = c4_form("bf16", precision="bf16")
     forms["upper_triangle"] = c4_form("upper_triangle", precision="split", upper_triangle=True)
+    # Phi and Psi stored as BF16 (the FP32 values rounded to nearest): half the output bytes
+    b16 = pkg.Context.alloc_out(n, n, yd.device, bf16=True)[:2]
+    forms["bf16_output"] = c4_form("bf16_output", out=b16, precision="split", output_bf16=True)
+    del b16
 
     # the batched form: 512 problems, m ~ U{8..200}, n log-uniform [256, 8192]
     spec = wl.c5_spec()
@@ -839,9 +846,8 @@ def run_ours(args, world, rank, local, pg):
         for name, e in errors.items():
             if name in forms:
                 forms[name]["error"] = e
-                forms[name]["within_tol"] = bool(
-                    e["rel_err_phi"] <= TOL.get("bf16" if name == "bf16" else "split")
-                    and e["rel_err_psi"] <= TOL.get("bf16" if name == "bf16" else "split"))
+                tol = TOL["bf16" if name in ("bf16", "bf16_output") else "split"]
+                forms[name]["within_tol"] = bool(e["rel_err_phi"] <= tol and e["rel_err_psi"] <= tol)
         x_ms = roofline["kernel_ms"]
         forms["speedup"] = {
             "split_vs_fp32_c4_step": round(forms["fp32"]["ms_per_step"] / ms_max, 2),

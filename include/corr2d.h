@@ -99,6 +99,18 @@ typedef enum {
  * 32 rows of the diagonal hold their mirrored values, the others are not
  * written.  Ignored for hetero problems. */
 #define CORR2D_FLAG_UPPER_TRIANGLE 8u
+/* Store Phi and Psi as BF16 (bfloat16: FP32's exponent range, 8 significant
+ * bits) instead of FP32: half the output bytes of a store-bound computation
+ * (the precision half of the output compaction that the symmetry facts of
+ * Sec. 3 and Sec. 4.3 motivate).  Each element is the FP32 result rounded to
+ * the nearest BF16 (ties to even): relative rounding error at most 2^-8
+ * (3.9e-3; about 2e-3 relative Frobenius error on a whole map).  phi and psi
+ * then point to 16-bit elements (passed as float* all the same), ldo counts
+ * 16-bit elements and must be a multiple of 8, and phi/psi stay 16-byte
+ * aligned.  Tensor-core precisions only (the FP32 path returns
+ * CORR2D_EUNSUPPORTED), and not for corr2d_compute_host or the
+ * allocation-free entry point, which return CORR2D_EUNSUPPORTED. */
+#define CORR2D_FLAG_OUTPUT_BF16 16u
 
 typedef struct {
   int ref_mode;       /* corr2d_ref_mode */
@@ -107,7 +119,7 @@ typedef struct {
   double norm;        /* <= 0 selects the default 1/(pi (m-1)) (Eq. disint2d) */
   double alpha;       /* 0: no scaling; 1: Pearson; 0.5: Pareto (Eqs. scale*) */
   int precision;      /* corr2d_precision */
-  unsigned flags;     /* CORR2D_FLAG_* */
+  unsigned flags;     /* CORR2D_FLAG_*; other bits are rejected with CORR2D_EINVAL */
 } corr2d_params;
 
 typedef struct corr2d_ctx corr2d_ctx; /* opaque: device, stream, workspace, tuning cache */
@@ -395,6 +407,7 @@ corr2d_status corr2d_get_kernel_info(corr2d_ctx* ctx, int* last_xspec, int* pair
  *   problem always runs on mirrored tiles (no tuner here), so its Phi is
  *   exactly symmetric and Psi exactly antisymmetric with a zero diagonal --
  *   what CORR2D_FLAG_EXACT_SYMMETRY asks of corr2d_compute.
+ *   CORR2D_FLAG_OUTPUT_BF16 is not available here (CORR2D_EUNSUPPORTED).
  * - Size limit: a problem needs about rows * rowbytes + twiddles, with rows =
  *   n1 for a homo problem (its two operands share one row set; the Hilbert
  *   variant keeps two: 2 n1) and n1 + n2 for a hetero one, rowbytes = 1 KB for

@@ -33,6 +33,7 @@ FLAG_NO_MIRROR = 1
 FLAG_EXACT_SYMMETRY = 2
 FLAG_HILBERT = 4
 FLAG_UPPER_TRIANGLE = 8
+FLAG_OUTPUT_BF16 = 16
 _PREC_BY_NAME = {"fp32": PREC_FP32, "split": PREC_SPLIT, "bf16": PREC_BF16}
 INTERP_LINEAR, INTERP_SPLINE = 0, 1
 _INTERP_BY_NAME = {"linear": INTERP_LINEAR, "spline": INTERP_SPLINE}
@@ -307,7 +308,7 @@ def _ptr(t):
 
 def make_params(precision="split", alpha=0.0, norm=0.0, ref1=None, ref2=None,
                 no_mirror=False, exact_symmetry=False, hilbert=False,
-                upper_triangle=False) -> corr2d_params:
+                upper_triangle=False, output_bf16=False) -> corr2d_params:
     p = corr2d_params_default()
     p.precision = _PREC_BY_NAME[precision] if isinstance(precision, str) else int(precision)
     p.alpha = float(alpha)
@@ -317,7 +318,8 @@ def make_params(precision="split", alpha=0.0, norm=0.0, ref1=None, ref2=None,
         p.ref1 = _ptr(ref1)
         p.ref2 = _ptr(ref2)
     p.flags = ((FLAG_NO_MIRROR if no_mirror else 0) | (FLAG_EXACT_SYMMETRY if exact_symmetry else 0)
-               | (FLAG_HILBERT if hilbert else 0) | (FLAG_UPPER_TRIANGLE if upper_triangle else 0))
+               | (FLAG_HILBERT if hilbert else 0) | (FLAG_UPPER_TRIANGLE if upper_triangle else 0)
+               | (FLAG_OUTPUT_BF16 if output_bf16 else 0))
     return p
 
 
@@ -373,22 +375,25 @@ class Context:
         return corr2d_get_kernel_info(self.handle)
 
     @staticmethod
-    def alloc_out(n1, n2, device, ld=None):
+    def alloc_out(n1, n2, device, ld=None, bf16=False):
         """Phi/Psi buffers whose rows start on 128-byte boundaries (ld a multiple of
-        32 floats): every stored 32-float box row is then one whole 128-byte line.
-        With rows only 16-byte aligned, half the rows of an odd-width matrix split
-        their lines into partial 32-byte sectors, which DRAM writes read-modify-write
-        (batches of ragged problems ran ~20 % slower)."""
+        32 floats, or 64 BF16 elements with bf16=True): every stored box row is then
+        one whole 128-byte line.  With rows only 16-byte aligned, half the rows of an
+        odd-width matrix split their lines into partial 32-byte sectors, which DRAM
+        writes read-modify-write (batches of ragged problems ran ~20 % slower)."""
         import torch
-        ldo = ld or (n2 + 31) // 32 * 32
-        phi = torch.empty((n1, ldo), dtype=torch.float32, device=device)
-        psi = torch.empty((n1, ldo), dtype=torch.float32, device=device)
+        q = 64 if bf16 else 32
+        ldo = ld or (n2 + q - 1) // q * q
+        dt = torch.bfloat16 if bf16 else torch.float32
+        phi = torch.empty((n1, ldo), dtype=dt, device=device)
+        psi = torch.empty((n1, ldo), dtype=dt, device=device)
         return phi, psi, ldo
 
     def compute(self, y1, y2=None, precision="split", alpha=0.0, norm=0.0, ref1=None, ref2=None,
                 no_mirror=False, out=None, want_sigma=False, exact_symmetry=False,
-                hilbert=False, upper_triangle=False):
-        """Phi, Psi (n1 x n2 views) of the m x n1 stack y1 (and y2, or homo)."""
+                hilbert=False, upper_triangle=False, output_bf16=False):
+        """Phi, Psi (n1 x n2 views) of the m x n1 stack y1 (and y2, or homo); BF16
+        tensors with output_bf16 (each the FP32 result rounded to nearest)."""
         import torch
         assert y1.is_cuda and y1.dtype == torch.float32 and y1.dim() == 2
         m, n1 = y1.shape
@@ -396,7 +401,7 @@ class Context:
             assert y2.is_cuda and y2.dtype == torch.float32 and y2.shape[0] == m
         n2 = n1 if y2 is None else y2.shape[1]
         if out is None:
-            phi, psi, ldo = self.alloc_out(n1, n2, y1.device)
+            phi, psi, ldo = self.alloc_out(n1, n2, y1.device, bf16=output_bf16)
         else:
             phi, psi = out
             ldo = phi.stride(0)
@@ -404,7 +409,7 @@ class Context:
         s2 = (torch.empty(n2, dtype=torch.float32, device=y1.device)
               if (want_sigma and y2 is not None) else None)
         params = make_params(precision, alpha, norm, ref1, ref2, no_mirror, exact_symmetry,
-                             hilbert, upper_triangle)
+                             hilbert, upper_triangle, output_bf16)
         corr2d_compute(self.handle, m, n1, _ptr(y1), y1.stride(0), n2, _ptr(y2),
                        y2.stride(0) if y2 is not None else 0, params, _ptr(phi), _ptr(psi), ldo,
                        _ptr(s1), _ptr(s2))
@@ -433,54 +438,59 @@ class Context:
         return out, dyn
 
     def batch(self, problems, precision="split", alpha=0.0, norm=0.0, no_mirror=False,
-              hilbert=False):
-        """problems: list of (y1, y2 or None, phi, psi) torch tensors (phi/psi n1 x ldo)."""
-        self.batch_plan(problems, precision, alpha, norm, no_mirror, hilbert).run()
+              hilbert=False, output_bf16=False):
+        """problems: list of (y1, y2 or None, phi, psi) torch tensors (phi/psi n1 x ldo,
+        BF16 with output_bf16)."""
+        self.batch_plan(problems, precision, alpha, norm, no_mirror, hilbert, output_bf16).run()
 
     def batch_plan(self, problems, precision="split", alpha=0.0, norm=0.0, no_mirror=False,
-                   hilbert=False) -> "BatchPlan":
+                   hilbert=False, output_bf16=False) -> "BatchPlan":
         """The descriptor array of a batch, marshalled once; ``run()`` submits it
         (repeated runs of the same list replay the library's recorded graph)."""
         return BatchPlan(self, problems, make_params(precision, alpha, norm, None, None,
-                                                     no_mirror, hilbert=hilbert))
+                                                     no_mirror, hilbert=hilbert,
+                                                     output_bf16=output_bf16))
 
     def compute_reduced(self, y1, y2, reduce, precision="split", alpha=0.0, norm=0.0,
-                        hilbert=False, ref1=None, ref2=None):
+                        hilbert=False, ref1=None, ref2=None, output_bf16=False):
         """Every reduce-th row and column of Phi and Psi (plot_corr2din3d's `reduce`)."""
         m, n1 = y1.shape
         n2 = n1 if y2 is None else y2.shape[1]
-        phi, psi, ldr = self.alloc_out(n1 // reduce, n2 // reduce, y1.device)
-        params = make_params(precision, alpha, norm, ref1, ref2, hilbert=hilbert)
+        phi, psi, ldr = self.alloc_out(n1 // reduce, n2 // reduce, y1.device, bf16=output_bf16)
+        params = make_params(precision, alpha, norm, ref1, ref2, hilbert=hilbert,
+                             output_bf16=output_bf16)
         corr2d_compute_reduced(self.handle, m, n1, _ptr(y1), y1.stride(0), n2, _ptr(y2),
                                y2.stride(0) if y2 is not None else 0, params, reduce, _ptr(phi),
                                _ptr(psi), ldr)
         return phi[:, :n2 // reduce], psi[:, :n2 // reduce]
 
     def compute_rows(self, y1, y2, row_begin, row_count, precision="split", alpha=0.0, norm=0.0,
-                     hilbert=False):
+                     hilbert=False, output_bf16=False):
         """Rows [row_begin, row_begin + row_count) of Phi and Psi (row_begin % 128 == 0)."""
         m, n1 = y1.shape
         n2 = n1 if y2 is None else y2.shape[1]
-        phi, psi, ldo = self.alloc_out(row_count, n2, y1.device)
-        params = make_params(precision, alpha, norm, hilbert=hilbert)
+        phi, psi, ldo = self.alloc_out(row_count, n2, y1.device, bf16=output_bf16)
+        params = make_params(precision, alpha, norm, hilbert=hilbert, output_bf16=output_bf16)
         corr2d_compute_rows(self.handle, m, n1, _ptr(y1), y1.stride(0), n2, _ptr(y2),
                             y2.stride(0) if y2 is not None else 0, params, row_begin, row_count,
                             _ptr(phi), _ptr(psi), ldo)
         return phi[:, :n2], psi[:, :n2]
 
     def compute_part(self, y1, y2, part, nparts, precision="split", alpha=0.0, norm=0.0,
-                     no_mirror=False, upper_triangle=False, hilbert=False, out=None):
+                     no_mirror=False, upper_triangle=False, hilbert=False, out=None,
+                     output_bf16=False):
         """Part `part` of `nparts` of the output tiles (and their mirrors) of Phi and Psi,
         written at their places in full n1 x n2 buffers; other elements are untouched."""
         m, n1 = y1.shape
         n2 = n1 if y2 is None else y2.shape[1]
         if out is None:
-            phi, psi, ldo = self.alloc_out(n1, n2, y1.device)
+            phi, psi, ldo = self.alloc_out(n1, n2, y1.device, bf16=output_bf16)
         else:
             phi, psi = out
             ldo = phi.stride(0)
         params = make_params(precision, alpha, norm, no_mirror=no_mirror,
-                             upper_triangle=upper_triangle, hilbert=hilbert)
+                             upper_triangle=upper_triangle, hilbert=hilbert,
+                             output_bf16=output_bf16)
         corr2d_compute_part(self.handle, m, n1, _ptr(y1), y1.stride(0), n2, _ptr(y2),
                             y2.stride(0) if y2 is not None else 0, params, part, nparts,
                             _ptr(phi), _ptr(psi), ldo)

@@ -217,6 +217,9 @@ corr2d_status check_params(corr2d_ctx* ctx, const corr2d_params* p, bool homo) {
     return fail(ctx, CORR2D_EINVAL, "alpha must be finite and >= 0");
   if (p->precision < CORR2D_PREC_FP32 || p->precision > CORR2D_PREC_BF16)
     return fail(ctx, CORR2D_EINVAL, "precision %d is not a corr2d_precision", p->precision);
+  const unsigned known = CORR2D_FLAG_NO_MIRROR | CORR2D_FLAG_EXACT_SYMMETRY | CORR2D_FLAG_HILBERT |
+                         CORR2D_FLAG_UPPER_TRIANGLE | CORR2D_FLAG_OUTPUT_BF16;
+  if (p->flags & ~known) return fail(ctx, CORR2D_EINVAL, "unknown flag bits 0x%x", p->flags & ~known);
   return CORR2D_OK;
 }
 
@@ -274,14 +277,18 @@ corr2d_status encode_operand(corr2d_ctx* ctx, CUtensorMap* tm, const void* base,
   return CORR2D_OK;
 }
 
+// Output map of Phi or Psi: 32 x 32 boxes, FP32 rows of 128 bytes (128-byte
+// swizzle) or, with CORR2D_FLAG_OUTPUT_BF16, BF16 rows of 64 bytes (64-byte
+// swizzle); ldo counts elements of the stored type.
 corr2d_status encode_output(corr2d_ctx* ctx, CUtensorMap* tm, float* base, int rows, int cols,
-                            long ldo) {
+                            long ldo, bool bf16 = false) {
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ldo * 4};
+  cuuint64_t strides[1] = {(cuuint64_t)ldo * (bf16 ? 2 : 4)};
   cuuint32_t box[2] = {32, 32};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = ctx->encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  CUresult r = ctx->encode(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                           2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           bf16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(ctx, CORR2D_ECUDA, "output tensor map encode failed (%d)", (int)r);
   return CORR2D_OK;
@@ -570,12 +577,15 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
     mkjob(y2, ld2, n2, r2, nullptr, opB, s2, sig2, hilbert ? wtab_b : wtab);
   }
   // the CTA-pair kernel computes whole 256-row pairs of tiles with bn = 128
-  const bool pair = nparts == 1 && tc.pair && tc.bn == TILE_N && ti_begin == 0 &&
+  // (both store FP32 only: BF16 output always takes the single-CTA kernel)
+  const bool fp32_out = !(p.flags & CORR2D_FLAG_OUTPUT_BF16);
+  const bool pair = fp32_out && nparts == 1 && tc.pair && tc.bn == TILE_N && ti_begin == 0 &&
                     ti_end == (n1 + TILE_M - 1) / TILE_M && out_row_tile0 == 0 &&
                     ctx->pair_clusters > 0;
   // the TMEM-operand kernel holds a row's stack-1 chunks in TMEM (at most
   // TA_MAX_CHUNKS) and also computes whole problems
-  const bool ta = nparts == 1 && tc.ta > 0 && !pair && pl.nch <= TA_MAX_CHUNKS && ti_begin == 0 &&
+  const bool ta = fp32_out && nparts == 1 && tc.ta > 0 && !pair && pl.nch <= TA_MAX_CHUNKS &&
+                  ti_begin == 0 &&
                   ti_end == (n1 + TILE_M - 1) / TILE_M && out_row_tile0 == 0;
   const int bn = ta ? TILE_N : tc.bn;
   XProblem xp;
@@ -584,8 +594,10 @@ corr2d_status enqueue_tc(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld
   if ((st = encode_operand(ctx, &xp.tmB, opB, pl.rowlen, n2, pair ? bn / 2 : bn, pl.planes)) !=
       CORR2D_OK)
     return st;
-  if ((st = encode_output(ctx, &xp.tmPhi, phi, out_rows, n2, ldo)) != CORR2D_OK) return st;
-  if ((st = encode_output(ctx, &xp.tmPsi, psi, out_rows, n2, ldo)) != CORR2D_OK) return st;
+  const bool obf = (p.flags & CORR2D_FLAG_OUTPUT_BF16) != 0;
+  if ((st = encode_output(ctx, &xp.tmPhi, phi, out_rows, n2, ldo, obf)) != CORR2D_OK) return st;
+  if ((st = encode_output(ctx, &xp.tmPsi, psi, out_rows, n2, ldo, obf)) != CORR2D_OK) return st;
+  xp.out_bf16 = obf ? 1 : 0;
   xp.s1 = s1;
   xp.s2 = s2;
   xp.norm = (float)default_norm(p, m);
@@ -993,6 +1005,8 @@ static corr2d_status validate_compute(corr2d_ctx* ctx, int m, int n1, const floa
   const bool tc = p.precision != CORR2D_PREC_FP32;
   if (!tc && m > MAX_M_FP32)
     return fail(ctx, CORR2D_EUNSUPPORTED, "the FP32 path supports m <= %d", MAX_M_FP32);
+  if ((p.flags & CORR2D_FLAG_OUTPUT_BF16) && !tc)
+    return fail(ctx, CORR2D_EUNSUPPORTED, "BF16 output runs the tensor-core precisions");
   if (p.flags & CORR2D_FLAG_HILBERT) {
     if (!tc)
       return fail(ctx, CORR2D_EUNSUPPORTED, "the Hilbert-transform variant runs the tensor-core precisions");
@@ -1004,6 +1018,10 @@ static corr2d_status validate_compute(corr2d_ctx* ctx, int m, int n1, const floa
       return fail(ctx, CORR2D_EUNSUPPORTED, "tensor-core precisions support m <= %d (use FP32)", MAX_M_TC);
     if (device_buffers && (ldo % 4 != 0 || ((uintptr_t)phi & 15) || ((uintptr_t)psi & 15)))
       return fail(ctx, CORR2D_EINVAL, "TMA stores need ldo %% 4 == 0 and 16-byte aligned phi/psi");
+    if ((p.flags & CORR2D_FLAG_OUTPUT_BF16) && ldo % 8 != 0)
+      return fail(ctx, CORR2D_EINVAL, "BF16 output needs ldo %% 8 == 0 (rows of 16-byte multiples)");
+    if ((p.flags & CORR2D_FLAG_OUTPUT_BF16) && !device_buffers)
+      return fail(ctx, CORR2D_EUNSUPPORTED, "BF16 output is for device buffers (not corr2d_compute_host)");
     if ((long)(n1 + TILE_M - 1) / TILE_M > 65535 || (long)(n2e + 63) / 64 > 65535)
       return fail(ctx, CORR2D_EUNSUPPORTED, "n too large for the tile index");
   }
@@ -1027,16 +1045,19 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
   // default; CORR2D_XSPEC=pair selects the CTA-pair kernel, =any lets the
   // tuner time both (the pair kernel measured slower on every workload tried).
   const char* xk = getenv("CORR2D_XSPEC");
-  const bool want_pair = xk && (strcmp(xk, "pair") == 0 || strcmp(xk, "any") == 0);
+  // (the CTA-pair and TMEM-operand kernels store FP32 only)
+  const bool obf = (p.flags & CORR2D_FLAG_OUTPUT_BF16) != 0;
+  const bool want_pair = !obf && xk && (strcmp(xk, "pair") == 0 || strcmp(xk, "any") == 0);
   const bool want_ta = xk && (strcmp(xk, "ta") == 0 || strcmp(xk, "any") == 0) &&
                        chunks_for(m, p.precision == CORR2D_PREC_SPLIT ? 2 : 1) <= TA_MAX_CHUNKS &&
-                       !(p.flags & CORR2D_FLAG_HILBERT);
+                       !(p.flags & CORR2D_FLAG_HILBERT) && !obf;
   const bool want_single = (!want_pair && !want_ta) || strcmp(xk, "any") == 0 ||
                            (want_pair && ctx->pair_clusters == 0);
   const int flag_bits = (int)(p.flags & (CORR2D_FLAG_NO_MIRROR | CORR2D_FLAG_EXACT_SYMMETRY |
-                                         CORR2D_FLAG_HILBERT | CORR2D_FLAG_UPPER_TRIANGLE));
+                                         CORR2D_FLAG_HILBERT | CORR2D_FLAG_UPPER_TRIANGLE |
+                                         CORR2D_FLAG_OUTPUT_BF16));
   auto key = std::make_tuple(m, n1, n2e, homo ? 1 : 0,
-                             flag_bits + 16 * p.precision +
+                             flag_bits + 32 * p.precision +
                                  256 * ((want_pair ? 1 : 0) + (want_single ? 2 : 0) +
                                         (want_ta ? 4 : 0)));
   // CORR2D_TILES=bn:mirror:group:chunk[:seg[:stages]] forces one tile choice
@@ -1189,11 +1210,15 @@ corr2d_status corr2d_compute_reduced(corr2d_ctx* ctx, int m, int n1, const float
     return fail(ctx, CORR2D_EINVAL, "reduce = %d must be in [1, min(n1, n2)]", reduce);
   const int n1r = n1 / reduce, n2r = n2 / reduce;
   DeviceGuard g(ctx->device);
+  // (the full map's checks see a stand-in leading dimension; ldr is checked below)
+  const long ld_full = std::max<long>(ldr, (n2 + 7) / 8 * 8);
   corr2d_status st = validate_compute(ctx, m, n1, y1, ld1, n2, homo ? nullptr : y2, ld2, p, phi_r,
-                                      psi_r, ldr < n2 ? n2 : ldr, true);
+                                      psi_r, ld_full, true);
   if (st != CORR2D_OK) return st;
   if (ldr < n2r || ldr % 4 != 0)
     return fail(ctx, CORR2D_EINVAL, "ldr must be >= n2 / reduce and a multiple of 4");
+  if ((p.flags & CORR2D_FLAG_OUTPUT_BF16) && ldr % 8 != 0)
+    return fail(ctx, CORR2D_EINVAL, "BF16 output needs ldr %% 8 == 0");
   if (p.precision == CORR2D_PREC_FP32)
     return fail(ctx, CORR2D_EUNSUPPORTED, "the reduced map runs the tensor-core precisions");
   if (p.ref_mode == CORR2D_REF_USER) {  // the references are sampled like the stacks
@@ -1517,8 +1542,10 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
       memset(&xp, 0, sizeof xp);
       if ((s2 = encode_operand(ctx, &xp.tmA, opA, pl.rowlen, q.n1, TILE_M, planes)) != CORR2D_OK) return s2;
       if ((s2 = encode_operand(ctx, &xp.tmB, opB, pl.rowlen, n2, bn, planes)) != CORR2D_OK) return s2;
-      if ((s2 = encode_output(ctx, &xp.tmPhi, q.phi, q.n1, n2, q.ldo)) != CORR2D_OK) return s2;
-      if ((s2 = encode_output(ctx, &xp.tmPsi, q.psi, q.n1, n2, q.ldo)) != CORR2D_OK) return s2;
+      const bool obf = (p.flags & CORR2D_FLAG_OUTPUT_BF16) != 0;
+      if ((s2 = encode_output(ctx, &xp.tmPhi, q.phi, q.n1, n2, q.ldo, obf)) != CORR2D_OK) return s2;
+      if ((s2 = encode_output(ctx, &xp.tmPsi, q.psi, q.n1, n2, q.ldo, obf)) != CORR2D_OK) return s2;
+      xp.out_bf16 = obf ? 1 : 0;
       xp.s1 = sc1; xp.s2 = sc2;
       xp.norm = (float)default_norm(p, q.m);
       xp.n1 = q.n1; xp.n2 = n2; xp.nchunks = pl.nch;

@@ -100,7 +100,8 @@ struct alignas(128) XProblem {
   int bn;              // nu2 columns per tile: 64 or 128
   int out_row_tile0;   // output rows are shifted up by out_row_tile0 * 128
   int upper_only;      // 1: mirrored problem storing only nu2 >= nu1 (no mirror boxes)
-  int pad_[2];
+  int out_bf16;        // 1: Phi and Psi stored as BF16 (tmPhi/tmPsi: BF16, 64-byte swizzle)
+  int pad_[1];
 };
 
 // One tile of the cross-spectrum kernel: problem index and tile coordinates.

@@ -16,7 +16,8 @@
 //               the products are hi*hi + hi*lo + lo*hi.
 //   warps 2..9  epilogue, two warps per TMEM lane quadrant (one for Phi, one
 //               for Psi): TMEM -> registers, scale, 128-byte-swizzled staging
-//               box, TMA store of 32x32 FP32 boxes.  For homo problems the
+//               box, TMA store of 32x32 FP32 boxes (BF16 boxes of 64-byte
+//               rows with CORR2D_FLAG_OUTPUT_BF16).  For homo problems the
 //               mirrored box is stored too (Phi symmetric, Psi antisymmetric),
 //               so only tiles with ti <= tj are computed.  Each warp stages
 //               its boxes in a ring of XS_EPI_SLOTS slots, one bulk group per
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
     const CUtensorMap* tm = nullptr;
     const float* s1p = nullptr;
     const float* s2p = nullptr;
-    int n1 = 0, n2 = 0, bn = 0, pmirror = 0, orow_off = 0, upper = 0;
+    int n1 = 0, n2 = 0, bn = 0, pmirror = 0, orow_off = 0, upper = 0, obf = 0;
     float norm = 0.f;
     for (;; ++lt) {
       const int ss = lt & (XS_SCHED - 1);
@@ -346,6 +347,7 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
         bn = pr->bn;
         pmirror = pr->mirror;
         upper = pr->upper_only;
+        obf = pr->out_bf16;
         orow_off = pr->out_row_tile0 * TILE_M;
         norm = pr->norm;
       }
@@ -418,7 +420,41 @@ __global__ void __launch_bounds__(XS_THREADS, 1)
         __syncwarp();
         uint8_t* slot0 = ring + slot * XS_BOX_BYTES;
         uint8_t* slot1 = ring + ((slot + 1) % XS_EPI_SLOTS) * XS_BOX_BYTES;
-        if (!tri) {
+        if (obf) {
+          // BF16 output: the same FP32 values rounded to nearest (ties to
+          // even), boxes of 32 rows x 64 bytes with the 64-byte swizzle
+          if (!tri) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              uint32_t w[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]);
+                w[e] = *reinterpret_cast<const uint32_t*>(&b2);
+              }
+              *(uint4*)(slot0 + sw64_off(lane, q)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+            if (mirror) {
+#pragma unroll
+              for (int i = 0; i < 32; ++i)
+                *(__nv_bfloat16*)(slot1 + sw64_off(i, lane >> 3) + (lane & 7) * 2) =
+                    __float2bfloat16_rn(sg * v[i]);
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+              if (c > lane) {
+                *(__nv_bfloat16*)(slot0 + sw64_off(lane, c >> 3) + (c & 7) * 2) =
+                    __float2bfloat16_rn(v[c]);
+                *(__nv_bfloat16*)(slot0 + sw64_off(c, lane >> 3) + (lane & 7) * 2) =
+                    __float2bfloat16_rn(sg * v[c]);
+              } else if (c == lane) {
+                *(__nv_bfloat16*)(slot0 + sw64_off(lane, c >> 3) + (c & 7) * 2) =
+                    __float2bfloat16_rn(half ? 0.f : v[c]);
+              }
+            }
+          }
+        } else if (!tri) {
           // box (rows row0.., cols col0..): row = lane, 8 swizzled 16-byte chunks
 #pragma unroll
           for (int c4 = 0; c4 < 8; ++c4)

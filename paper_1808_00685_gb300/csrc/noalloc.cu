@@ -176,6 +176,11 @@ extern "C" corr2d_status corr2d_compute_noalloc(int device, void* cuda_stream, i
     return say(msg, msg_len, CORR2D_EINVAL, "user reference mode needs ref1 (and ref2)");
   if (!std::isfinite(p.norm) || !(p.alpha >= 0.0) || !std::isfinite(p.alpha))
     return say(msg, msg_len, CORR2D_EINVAL, "norm and alpha must be finite, alpha >= 0");
+  if (p.flags & CORR2D_FLAG_OUTPUT_BF16)
+    return say(msg, msg_len, CORR2D_EUNSUPPORTED, "BF16 output needs corr2d_compute");
+  if (p.flags & ~(CORR2D_FLAG_NO_MIRROR | CORR2D_FLAG_EXACT_SYMMETRY | CORR2D_FLAG_HILBERT |
+                  CORR2D_FLAG_UPPER_TRIANGLE))
+    return say(msg, msg_len, CORR2D_EINVAL, "unknown flag bits");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev ||
       device >= kMaxDevices) {

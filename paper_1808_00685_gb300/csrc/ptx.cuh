@@ -301,6 +301,13 @@ __device__ __forceinline__ uint32_t sw128_off(uint32_t r, uint32_t c) {
   return r * 128u + ((c ^ (r & 7u)) << 4);
 }
 
+// Byte offset of 16-byte chunk c (0..3) of row r in a tile of 64-byte rows
+// with the 64-byte swizzle (address bits 4-5 XOR bits 7-8); the tile starts
+// at a 512-byte boundary.
+__device__ __forceinline__ uint32_t sw64_off(uint32_t r, uint32_t c) {
+  return r * 64u + ((c ^ ((r >> 1) & 3u)) << 4);
+}
+
 __device__ __forceinline__ bool elect_lane0() { return (threadIdx.x & 31u) == 0; }
 
 // ------------------------------------------------ CTA pairs (cluster of two)

@@ -170,6 +170,12 @@ def test_noalloc_refuses_what_it_cannot_do(pkg):
                                    pkg.make_params("split"), phi.data_ptr(), phi.data_ptr(), 40000)
     assert ei.value.status == pkg.EUNSUPPORTED
     assert "scratch" in str(ei.value)
+    # BF16 output needs corr2d_compute
+    with pytest.raises(pkg.Corr2dError) as ei:
+        pkg.corr2d_compute_noalloc(0, stream, 16, 64, y.data_ptr(), 64, 0, None, 0,
+                                   pkg.make_params("split", output_bf16=True), phi.data_ptr(),
+                                   phi.data_ptr(), 64)
+    assert ei.value.status == pkg.EUNSUPPORTED
     # the Hilbert variant stops at m = 256, the FP32 path needs a context
     y = torch.zeros((300, 64), dtype=torch.float32, device="cuda")
     out = torch.empty((64, 64), dtype=torch.float32, device="cuda")
