@@ -1621,10 +1621,12 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
   // tuner: time the batch graph for each candidate, keep the fastest:
   // tile width (bn = 64 below a problem size) x run length per CTA x the
   // frequency count up to which homo problems use full tiles
-  const int thresholds[] = {0, 1024, 2048};
+  // (bn = 64 below n = 2048 lost to both others on every batch timed; 64 x 64
+  // super-blocks are what the single-problem tuner takes for large homo problems)
+  const int thresholds[] = {0, 1024};
   const int chunks[] = {1, 4};
   const int full_kps[] = {0, 64};
-  const int groups[] = {0, 8};
+  const int groups[] = {0, 8, 64};
   const int nfull = may_unmirror ? 2 : 1;
   int best_thr = 0, best_chunk = 1, best_full = 0, best_group = 0;
   if (!getenv("CORR2D_NO_TUNE")) {
@@ -1633,8 +1635,8 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hp,
     CUDA_TRY(ctx, cudaEventCreate(&e1));
     float best = 1e30f;
     for (int cand = 0; cand < 12 * nfull; ++cand) {
-      const int thr = thresholds[cand % 3], chunk = chunks[(cand / 3) % 2];
-      const int group = groups[(cand / 6) % 2];
+      const int thr = thresholds[cand % 2], chunk = chunks[(cand / 2) % 2];
+      const int group = groups[(cand / 4) % 3];
       const int full_kp = full_kps[cand / 12];
       BatchExecs ex;
       if ((st = make_graph(thr, chunk, full_kp, group, &ex)) != CORR2D_OK) {
