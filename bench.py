@@ -459,9 +459,10 @@ def error_of(got, want):
 
 
 # ---------------------------------------------------------------- CPU oracle
-def cpu_oracle_rate(y, n_sample=0, alpha=0.0, target_s=15.0):
+def cpu_oracle_rate(y, n_sample=0, alpha=0.0, target_s=15.0, single=False):
     """The FP64 oracle as it stands, all host threads, on the first n_sample
-    spectral variables of the same stack (homo).  Returns (elems/s, info)."""
+    spectral variables of the same stack (homo), and on one thread on a smaller
+    sample (info["single_thread"]).  Returns (elems/s, info)."""
     import oracle
     threads = oracle.max_threads()
     m = y.shape[0]
@@ -481,10 +482,20 @@ def cpu_oracle_rate(y, n_sample=0, alpha=0.0, target_s=15.0):
     t0 = time.perf_counter()
     oracle.corr2d(ys, alpha=alpha, nthreads=threads)
     dt = time.perf_counter() - t0
-    return n_sample * n_sample / dt, dict(
-        kind="oracle", cores=threads,
-        sample=f"homo m={m}, first {n_sample} spectral variables of the same stack "
-               f"({n_sample * n_sample} outputs, {dt:.1f} s)", seconds=dt)
+    info = dict(kind="oracle", cores=threads,
+                sample=f"homo m={m}, first {n_sample} spectral variables of the same stack "
+                       f"({n_sample * n_sample} outputs, {dt:.1f} s)", seconds=dt)
+    if single:
+        # one host thread too, on a sample sized for ~4 s (the cost grows as n^2)
+        n1 = int(max(128, n_sample * math.sqrt(4.0 / max(dt, 1e-3)) / math.sqrt(threads)))
+        n1 = min(n1, n_sample)
+        t1 = time.perf_counter()
+        oracle.corr2d(y[:, :n1].copy(), alpha=alpha, nthreads=1)
+        dt1 = time.perf_counter() - t1
+        info["single_thread"] = {"value": n1 * n1 / dt1, "cores": 1,
+                                 "sample": f"homo m={m}, first {n1} spectral variables "
+                                           f"({n1 * n1} outputs, {dt1:.1f} s)"}
+    return n_sample * n_sample / dt, info
 
 
 def oracle_at(y1, y2, rows, cols, alpha=0.0):
@@ -507,7 +518,7 @@ def cpu_baseline_leg(args, y, alpha, checks):
     errors are computed.  Returns (cpu_baseline dict or None, errors by form)."""
     cpu = None
     if y is not None and not args.no_cpu_baseline:
-        rate, info = cpu_oracle_rate(y, args.cpu_sample_n, alpha)
+        rate, info = cpu_oracle_rate(y, args.cpu_sample_n, alpha, single=True)
         cpu = {"value": rate, "unit": UNIT, **{k: v for k, v in info.items() if k != "seconds"}}
     errors = {}
     t0 = time.perf_counter()
