@@ -348,7 +348,10 @@ typedef struct {
  * Many independent correlations of uneven m, n1, n2: one batched DFT launch
  * and one persistent cross-spectrum launch over a cost-ordered tile list, with
  * per-problem tile shapes from the tuner; the launches are captured once in a
- * CUDA graph per batch layout and replayed.  host_problems is a host array of
+ * CUDA graph per batch layout and replayed, the cross-spectrum launch
+ * programmatically dependent on the DFT launch (its setup overlaps the DFT's
+ * last wave; while profiling is on, the two run as separate graphs with the
+ * timing events between them).  host_problems is a host array of
  * `count` descriptors.  shared_params (NULL = defaults) applies to every
  * problem; its ref_mode must be CORR2D_REF_MEAN and its precision a
  * tensor-core precision.  A call whose problem list and parameters equal the
@@ -362,7 +365,9 @@ corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* hos
 /* Per-kernel timing of the last corr2d_compute / corr2d_batch call on this
  * context, from CUDA events recorded on the context's stream around each
  * kernel while profiling is on (the paper profiles its own steps the same
- * way, Sec. 4.3).  corr2d_get_timings waits for those events.
+ * way, Sec. 4.3).  corr2d_get_timings waits for those events.  The events
+ * serialise the two launches, which otherwise overlap (programmatic dependent
+ * launch), so a call with profiling on can take a few microseconds longer.
  *   prep_ms   reference, centering, sigma and DFT kernel(s)
  *   xspec_ms  cross-spectrum kernel
  * Returns EINVAL when profiling is off or nothing was recorded yet. */
