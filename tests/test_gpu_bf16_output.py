@@ -209,3 +209,19 @@ def test_bf16_output_is_refused_where_it_cannot_be_stored(pkg, ctx):
         pkg.corr2d_compute(ctx.handle, 16, 200, d.data_ptr(), 200, 0, None, 0, p,
                            phi.data_ptr(), psi.data_ptr(), 200)
     assert ei.value.status == pkg.EINVAL
+
+
+@pytest.mark.parametrize("m,n1,n2", [(2, 1, None), (2, 7, None), (3, 33, None), (4, 129, None),
+                                     (5, 128, None), (16, 257, None), (130, 131, None),
+                                     (257, 140, None), (512, 64, None), (9, 1, 40), (33, 70, 1),
+                                     (65, 300, 77)])
+def test_bf16_output_on_ragged_and_extreme_shapes(ctx, m, n1, n2):
+    """Single variables, one step past a tile, the largest m: every BF16 element is
+    the FP32 element rounded (boxes cut at ragged edges, the m = 2 zero map)."""
+    y1 = workloads.random_stack(m, n1, seed=m * 1000 + n1, offset=3.0)
+    y2 = None if n2 is None else workloads.random_stack(m, n2, seed=m * 77 + n2, offset=-1.0)
+    d1, d2 = _dev(y1), None if y2 is None else _dev(y2)
+    p32, q32 = ctx.compute(d1, d2)
+    p16, q16 = ctx.compute(d1, d2, output_bf16=True)
+    ctx.synchronize()
+    assert _same_bits(p16, p32) and _same_bits(q16, q32), (m, n1, n2)

@@ -54,6 +54,8 @@ CASES = [
     ("homo m=33 n=517 bf16", (33, 517, None), {"precision": "bf16"}),
     ("homo m=40 n=600 Hilbert", (40, 600, None), {"hilbert": True}),
     ("homo m=96 n=1500 upper triangle", (96, 1500, None), {"upper_triangle": True}),
+    ("homo m=3 n=33", (3, 33, None), {}),
+    ("hetero m=257 140 x 1", (257, 140, 1), {}),
 ]
 
 
@@ -86,7 +88,8 @@ def test_overlapped_and_serialised_launches_are_bit_identical(pkg, name, shape, 
     for a, b in zip(got["off"], got["always"]):
         assert np.array_equal(a, b), name
     if name.startswith("hetero"):
-        ophi, opsi, _, _ = oracle.corr2d(y1, y2, alpha=0.5, nthreads=oracle.max_threads())
+        ophi, opsi, _, _ = oracle.corr2d(y1, y2, alpha=kw.get("alpha", 0.0),
+                                         nthreads=oracle.max_threads())
         phi, psi = got["always"]
         assert np.linalg.norm(phi - ophi) / np.linalg.norm(ophi) <= 1e-5
         assert np.linalg.norm(psi - opsi) / np.linalg.norm(opsi) <= 1e-5
