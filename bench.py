@@ -9,9 +9,9 @@ cross-spectrum kernel.  Prints one JSON line (rank 0).
 
 The default run also times the comparison forms the metric names, on the same
 inputs, L2 flush and CUDA-event timing ("forms" in the JSON line): the plain
-FP32 GPU path and BF16 on the same problem, the upper-triangle output, and the
-batched form (512 problems of uneven m, n1, n2) against one call per problem
-and against the FP32 path per problem.  Their errors against the FP64 oracle,
+FP32 GPU path and BF16 operands on the same problem, the upper-triangle and the
+BF16 output, and the batched form (512 problems of uneven m, n1, n2) against one
+call per problem and against the FP32 path per problem.  Their errors against the FP64 oracle,
 on sampled outputs, come from the CPU-baseline leg, the one place the oracle
 runs.
 
@@ -22,9 +22,12 @@ Under torchrun the homo workloads (c4, c2) are split over the ranks by output
 tiles (corr2d_compute_part: each GPU a balanced, contiguous part of the
 mirrored tile list, written into its own buffer; strong scaling, no data-path
 collective): the value is the problem's outputs divided by the slowest rank's
-time.  The other workloads run one independent problem per rank (weak
-scaling): all ranks' outputs divided by the slowest rank's time.  --impl reference times the FP64
-CPU oracle on the host cores on a bounded sample of the same workload.
+time.  The batched workload (c5) is split by problem (corr2d_plan_batch_part: a
+cost-balanced share of the 512 problems per GPU, each rank one corr2d_batch call;
+strong scaling, no collective).  The other workloads run one independent problem
+per rank (weak scaling): all ranks' outputs divided by the slowest rank's time.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample
+of the same workload.
 """
 from __future__ import annotations
 
@@ -735,6 +738,20 @@ def run_ours(args, world, rank, local, pg):
         y = raw.y1
     else:
         spec = inputs
+        outputs = spec.total_outputs
+        if world > 1 and not (args.no_batch or args.precision == "fp32"):
+            # one batch over several GPUs: each rank runs corr2d_batch on its cost-balanced
+            # share of the problems (strong scaling, no data-path collective)
+            shapes = [(p.m, p.n1, p.n2, p.homo) for p in spec.problems]
+            sel = pkg.plan_batch_part(shapes, rank, world)
+            if not sel:
+                raise SystemExit(f"rank {rank} of {world}: no problems in its part")
+            strong = True
+            scaling = "strong"
+            parallelism = (f"strong: the batch split by problem over {world} GPUs "
+                           f"(corr2d_plan_batch_part, cost-balanced; this rank {len(sel)} of "
+                           f"{len(spec.problems)} problems), no collective")
+            spec = wl.BatchSpec(problems=[spec.problems[i] for i in sel])
         ins = wl.batch_inputs(spec)
         probs = []
         for (y1, y2), p in zip(ins, spec.problems):
@@ -742,7 +759,6 @@ def run_ours(args, world, rank, local, pg):
             d2 = None if y2 is None else torch.from_numpy(y2).to(device)
             ph, ps, _ = pkg.Context.alloc_out(p.n1, p.n2, device)
             probs.append((d1, d2, ph, ps))
-        outputs = spec.total_outputs
         if args.no_batch or args.precision == "fp32":
             # one library call per problem (the FP32 path has no batched form)
             launches_per_step = sum(2 if y2 is None else 3 if args.precision == "fp32" else 2

@@ -362,6 +362,30 @@ typedef struct {
 corr2d_status corr2d_batch(corr2d_ctx* ctx, int count, const corr2d_problem* host_problems,
                            const corr2d_params* shared_params);
 
+/*
+ * Host-only (no GPU, no context; the paper runs one problem at a time and has
+ * no counterpart): which problems of a batch go to part `part` of `nparts`,
+ * for running one batch over several GPUs -- one process per GPU, each calling
+ * corr2d_batch on its part, no communication.  Problem i has m[i] perturbation
+ * steps, n1[i] spectral variables in stack 1 and n2[i] in stack 2 (n2[i] == 0:
+ * homo, stack 2 = stack 1).  Its cost, in units of one output pair, is
+ *   n1 n2 + 3 m (n1 + n2)      (homo: n1 n1 + 3 m n1),
+ * the stored pair against the DFT work per input element (about 3 pairs' worth
+ * each: the batch of 512 ragged problems took 1.3 ps per output pair in its
+ * cross-spectrum launch and 4.1 ps per input element in its DFT launch on one
+ * GB300).  Problems are taken by decreasing cost (ties: lower index first) and
+ * each goes to the part with the smallest total so far (ties: lower part), so
+ * the largest part exceeds the mean by less than the largest single cost.  The
+ * assignment depends on the shapes alone, so every process computes the same
+ * one.  *count receives the number of problems of the part; indices, when not
+ * NULL, receives their indices in increasing order (room for cap ints).
+ * EINVAL for count < 0, NULL arrays with count > 0, a bad part, a problem with
+ * m < 2, n1 < 1 or n2 < 0, or cap < *count; corr2d_last_error(NULL) describes
+ * the failure.
+ */
+corr2d_status corr2d_plan_batch_part(int count, const int* m, const int* n1, const int* n2,
+                                     int part, int nparts, int* indices, int cap, int* count_out);
+
 /* Per-kernel timing of the last corr2d_compute / corr2d_batch call on this
  * context, from CUDA events recorded on the context's stream around each
  * kernel while profiling is on (the paper profiles its own steps the same

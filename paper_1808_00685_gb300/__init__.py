@@ -45,7 +45,7 @@ EXPORTED_SYMBOLS = (
     "corr2d_get_timings", "corr2d_compute_noalloc", "corr2d_preprocess_perturbation",
     "corr2d_compute_rows", "corr2d_compute_reduced", "corr2d_interpolate_perturbation",
     "corr2d_get_kernel_info", "corr2d_measure_fp32_peak", "corr2d_compute_part",
-    "corr2d_plan_part",
+    "corr2d_plan_part", "corr2d_plan_batch_part",
 )
 XSPEC_NONE, XSPEC_TC, XSPEC_TC_PAIR, XSPEC_FP32, XSPEC_TC_TA = range(5)
 
@@ -117,6 +117,9 @@ def load(path: str | None = None):
                                         i, i, vp, vp, ctypes.c_long]),
             "corr2d_plan_part": (i, [i, i, i, ctypes.c_uint, i, i, ctypes.POINTER(i), i,
                                      ctypes.POINTER(i)]),
+            "corr2d_plan_batch_part": (i, [i, ctypes.POINTER(i), ctypes.POINTER(i),
+                                           ctypes.POINTER(i), i, i, ctypes.POINTER(i), i,
+                                           ctypes.POINTER(i)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -214,6 +217,22 @@ def corr2d_plan_part(n1: int, n2: int, homo: bool, flags: int, part: int, nparts
     _check(None, lib.corr2d_plan_part(n1, n2, 1 if homo else 0, flags, part, nparts, buf,
                                       cnt.value, ctypes.byref(cnt)))
     return [(buf[2 * i], buf[2 * i + 1]) for i in range(cnt.value)]
+
+
+def plan_batch_part(shapes, part: int, nparts: int):
+    """Indices (increasing) of the problems of a batch that go to part `part` of
+    `nparts` (host only; corr2d_plan_batch_part's cost-balanced split).  shapes:
+    (m, n1, n2, homo) per problem; a homo problem's n2 is ignored."""
+    lib = load()
+    k = len(shapes)
+    arr = lambda vals: (ctypes.c_int * max(k, 1))(*vals)
+    m = arr([s[0] for s in shapes])
+    n1 = arr([s[1] for s in shapes])
+    n2 = arr([0 if s[3] else s[2] for s in shapes])
+    cnt = ctypes.c_int()
+    out = (ctypes.c_int * max(k, 1))()
+    _check(None, lib.corr2d_plan_batch_part(k, m, n1, n2, part, nparts, out, k, ctypes.byref(cnt)))
+    return [out[i] for i in range(cnt.value)]
 
 
 def shard_rows(n1: int, world: int, rank: int, tile: int = 128):

@@ -1289,6 +1289,47 @@ corr2d_status corr2d_plan_part(int n1, int n2, int homo, unsigned flags, int par
   return CORR2D_OK;
 }
 
+corr2d_status corr2d_plan_batch_part(int count, const int* m, const int* n1, const int* n2,
+                                     int part, int nparts, int* indices, int cap,
+                                     int* count_out) {
+  if (!count_out) return fail(nullptr, CORR2D_EINVAL, "count_out is NULL");
+  *count_out = 0;
+  if (count < 0) return fail(nullptr, CORR2D_EINVAL, "count = %d", count);
+  if (count > 0 && (!m || !n1 || !n2)) return fail(nullptr, CORR2D_EINVAL, "NULL shape arrays");
+  if (nparts < 1 || part < 0 || part >= nparts)
+    return fail(nullptr, CORR2D_EINVAL, "part %d of %d is not a part", part, nparts);
+  std::vector<double> cost(count);
+  for (int i = 0; i < count; ++i) {
+    if (m[i] < 2 || n1[i] < 1 || n2[i] < 0)
+      return fail(nullptr, CORR2D_EINVAL, "problem %d: m = %d, n1 = %d, n2 = %d", i, m[i], n1[i],
+                  n2[i]);
+    const double a = n1[i], b = n2[i] == 0 ? n1[i] : n2[i];
+    const double vars = n2[i] == 0 ? a : a + b;  // input variables: one stack for homo
+    cost[i] = a * b + 3.0 * m[i] * vars;
+  }
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<double> load(nparts, 0.0);
+  std::vector<int> mine;
+  for (int i : order) {
+    int best = 0;
+    for (int q = 1; q < nparts; ++q)
+      if (load[q] < load[best]) best = q;
+    load[best] += cost[i];
+    if (best == part) mine.push_back(i);
+  }
+  std::sort(mine.begin(), mine.end());
+  *count_out = (int)mine.size();
+  if (indices) {
+    if (cap < (int)mine.size())
+      return fail(nullptr, CORR2D_EINVAL, "part %d has %d problems; cap is %d", part,
+                  (int)mine.size(), cap);
+    for (size_t k = 0; k < mine.size(); ++k) indices[k] = mine[k];
+  }
+  return CORR2D_OK;
+}
+
 corr2d_status corr2d_compute_part(corr2d_ctx* ctx, int m, int n1, const float* y1, int ld1,
                                   int n2, const float* y2, int ld2, const corr2d_params* params,
                                   int part, int nparts, float* phi, float* psi, long ldo) {

@@ -1,13 +1,14 @@
 """Multi-process (world size 2, gloo on CPU) coverage of the multi-GPU logic.
 
-Two ways to use several GPUs: independent problems per rank (the only
+Three ways to use several GPUs: independent problems per rank (the only
 cross-rank operations are the timing barrier and the max-over-ranks
-reduction), and one problem split by output tiles (corr2d_compute_part: each
-rank computes a balanced, contiguous part of the mirrored tile list and its
-mirrored blocks; the parts cover the map exactly once).  The partition is host
-logic (corr2d_plan_part), so it is checked here without a GPU: coverage for
-many shapes, and two gloo ranks that compute their parts with the oracle and
-gather the full map."""
+reduction), one problem split by output tiles (corr2d_compute_part: each rank
+computes a balanced, contiguous part of the mirrored tile list and its
+mirrored blocks; the parts cover the map exactly once), and one batch split by
+problem (corr2d_plan_batch_part: a cost-balanced assignment, each rank running
+corr2d_batch on its problems).  The partitions are host logic, so they are
+checked here without a GPU: coverage and balance for many shapes, and two gloo
+ranks that compute their parts with the oracle and gather the results."""
 import json
 import os
 import subprocess
@@ -160,3 +161,104 @@ def test_two_gloo_ranks_compute_their_tile_parts_and_gather_the_full_map(tmp_pat
     _lib()
     mp.spawn(_part_worker, args=(2, 29517, str(tmp_path)), nprocs=2, join=True)
     assert open(tmp_path / "result.txt").read() == repr((True, True, True))
+
+
+def _batch_cost(m, n1, n2, homo):
+    """Cost of one problem in units of one output pair (the documented model)."""
+    return n1 * (n1 if homo else n2) + 3 * m * (n1 if homo else n1 + n2)
+
+
+@pytest.mark.parametrize("nparts", [1, 2, 3, 4, 8, 600])
+def test_batch_parts_cover_every_problem_once_and_balance_cost(nparts):
+    import workloads
+    import paper_1808_00685_gb300 as pkg
+    _lib()
+    spec = workloads.c5_spec()
+    shapes = [(p.m, p.n1, p.n2, p.homo) for p in spec.problems]
+    parts = [pkg.plan_batch_part(shapes, r, nparts) for r in range(nparts)]
+    flat = sorted(i for part in parts for i in part)
+    assert flat == list(range(len(shapes)))  # every problem in exactly one part
+    assert all(part == sorted(part) for part in parts)
+    cost = [_batch_cost(*s) for s in shapes]
+    loads = [sum(cost[i] for i in part) for part in parts]
+    mean = sum(cost) / nparts
+    assert max(loads) - mean < max(cost)  # greedy bound: less than one problem above the mean
+    # the same shapes give the same split (every process computes it alone)
+    assert parts == [pkg.plan_batch_part(shapes, r, nparts) for r in range(nparts)]
+
+
+def test_batch_parts_follow_the_greedy_rule_on_a_small_list():
+    """Costs 1000, 400, 250, 160 over 2 parts: by decreasing cost, each to the lighter
+    part -> {0} and {1, 2, 3} (1000 against 810)."""
+    import paper_1808_00685_gb300 as pkg
+    _lib()
+    # homo n1 = 10: cost = 100 + 30 m
+    shapes = [(30, 10, 0, True), (10, 10, 0, True), (5, 10, 0, True), (2, 10, 0, True)]
+    costs = [_batch_cost(*s) for s in shapes]
+    assert costs == [1000, 400, 250, 160]
+    assert pkg.plan_batch_part(shapes, 0, 2) == [0]
+    assert pkg.plan_batch_part(shapes, 1, 2) == [1, 2, 3]
+    # ties go to the lower index, then to the lower part
+    same = [(4, 8, 0, True)] * 5
+    assert pkg.plan_batch_part(same, 0, 2) == [0, 2, 4]
+    assert pkg.plan_batch_part(same, 1, 2) == [1, 3]
+
+
+def test_batch_part_arguments_are_checked():
+    import paper_1808_00685_gb300 as pkg
+    _lib()
+    with pytest.raises(pkg.Corr2dError):
+        pkg.plan_batch_part([(8, 10, 0, True)], 2, 2)  # part out of range
+    with pytest.raises(pkg.Corr2dError):
+        pkg.plan_batch_part([(1, 10, 0, True)], 0, 1)  # m < 2
+    with pytest.raises(pkg.Corr2dError):
+        pkg.plan_batch_part([(8, 0, 0, True)], 0, 1)  # n1 < 1
+    assert pkg.plan_batch_part([], 0, 3) == []
+
+
+def _batch_part_worker(rank, world, port, out):
+    """One rank: the oracle on its problems of a small ragged batch; the ranks' results
+    are gathered with gloo and rank 0 checks that every problem was computed once and
+    equals one oracle call over the whole list."""
+    import numpy as np
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import oracle
+    import paper_1808_00685_gb300 as pkg
+    import workloads
+    pkg.load()
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    spec = workloads.c5_spec(count=9, seed=5, m_lo=3, m_hi=20, n_lo=8, n_hi=60)
+    ins = workloads.batch_inputs(spec, nbands=3)
+    shapes = [(p.m, p.n1, p.n2, p.homo) for p in spec.problems]
+    mine = {}
+    for i in pkg.plan_batch_part(shapes, rank, world):
+        y1, y2 = ins[i]
+        phi, psi, _, _ = oracle.corr2d(y1, y2)
+        mine[i] = (phi.tolist(), psi.tolist())
+    got = [None] * world
+    dist.all_gather_object(got, mine)
+    if rank == 0:
+        merged = {}
+        twice = False
+        for d in got:
+            for i, v in d.items():
+                twice = twice or i in merged
+                merged[i] = v
+        ok = not twice and sorted(merged) == list(range(len(shapes)))
+        for i, (y1, y2) in enumerate(ins):
+            phi, psi, _, _ = oracle.corr2d(y1, y2)
+            ok = ok and np.array_equal(np.array(merged[i][0]), phi)
+            ok = ok and np.array_equal(np.array(merged[i][1]), psi)
+        with open(os.path.join(out, "result.txt"), "w") as f:
+            f.write(repr(ok))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_compute_their_batch_parts_and_gather_every_problem(tmp_path):
+    import torch.multiprocessing as mp
+    _lib()
+    mp.spawn(_batch_part_worker, args=(2, 29519, str(tmp_path)), nprocs=2, join=True)
+    assert open(tmp_path / "result.txt").read() == "True"
