@@ -7,8 +7,10 @@ whichever CTA computes it.  So a context with the overlap forced on
 (CORR2D_PDL=always) and one with it off (CORR2D_PDL=off) give identical Phi
 and Psi, and the batch's graph holding both launches with the
 programmatic edge (replayed when no timings are recorded) gives what its two
-separate graphs give (replayed when they are).  One case is also held to the
-FP64 oracle at the parity tolerance (1e-5 relative Frobenius error).
+separate graphs give (replayed when they are).  Both contexts take the tuner's
+first tile candidate, so that they run the same tile layout.  Every FT case is
+also held to the FP64 oracle at the parity tolerance (1e-5 relative Frobenius
+error; 1e-2 with BF16 operands).
 """
 import os
 
@@ -20,6 +22,20 @@ import workloads
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def one_tile_choice():
+    """Both contexts take the same tile layout (the tuner's first candidate): each
+    context tunes on its own, and full and mirrored tiles may differ in the last FP32
+    bit of the mirrored half."""
+    old = os.environ.get("CORR2D_NO_TUNE")
+    os.environ["CORR2D_NO_TUNE"] = "1"
+    yield
+    if old is None:
+        del os.environ["CORR2D_NO_TUNE"]
+    else:
+        os.environ["CORR2D_NO_TUNE"] = old
 
 
 @pytest.fixture(scope="module")
@@ -87,12 +103,14 @@ def test_overlapped_and_serialised_launches_are_bit_identical(pkg, name, shape, 
             ctx.close()
     for a, b in zip(got["off"], got["always"]):
         assert np.array_equal(a, b), name
-    if name.startswith("hetero"):
+    if not kw.get("hilbert"):  # the overlapped launch against the oracle, too
         ophi, opsi, _, _ = oracle.corr2d(y1, y2, alpha=kw.get("alpha", 0.0),
                                          nthreads=oracle.max_threads())
         phi, psi = got["always"]
-        assert np.linalg.norm(phi - ophi) / np.linalg.norm(ophi) <= 1e-5
-        assert np.linalg.norm(psi - opsi) / np.linalg.norm(opsi) <= 1e-5
+        tol = 1e-2 if kw.get("precision") == "bf16" else 1e-5
+        if np.linalg.norm(ophi) > 0:
+            assert np.linalg.norm(phi - sel(ophi)) / np.linalg.norm(sel(ophi)) <= tol, name
+            assert np.linalg.norm(psi - sel(opsi)) / np.linalg.norm(sel(opsi)) <= tol, name
 
 
 def test_batch_graphs_with_and_without_timing_events_are_bit_identical(pkg):
