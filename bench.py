@@ -5,7 +5,10 @@ Default workload: homo correlation, m = 256 perturbation steps, n = 32768
 spectral variables, FP16 hi/lo split precision (32768^2 complex outputs,
 8.6 GB of Phi and Psi per step).  A step is one corr2d_compute call: the
 tcgen05 DFT kernel (reference, centering, sigma, transform), then the tcgen05
-cross-spectrum kernel.  Prints one JSON line (rank 0).
+cross-spectrum kernel.  Prints one JSON line (rank 0).  Its roofline is that of the
+cross-spectrum kernel against HBM (the measured copy bandwidth), with the tensor
+roofline (its tcgen05 flops against the measured BF16 peak) beside it; the one with
+the larger fraction, the binding one, leads.
 
 The default run also times the comparison forms the metric names, on the same
 inputs, L2 flush and CUDA-event timing ("forms" in the JSON line): the plain
@@ -196,6 +199,36 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def measured_tensor_peak():
+    """Dense BF16 tensor throughput (TFLOP/s) of MEASURED_PEAKS.json, the burst figure;
+    the split products are FP16 MMAs, whose nominal dense rate equals BF16's."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (bf16 burst)"
+    return 1900.0, "fallback"
+
+
+def tensor_flops(m, precision, pairs):
+    """Tensor-core flops of the cross-spectrum over `pairs` output pairs: 8 K' per pair (the
+    two real dot products of length 2 K'), three products each for the FP16 hi/lo split."""
+    kp = (m - 1) // 2 + 1
+    return 8.0 * kp * pairs * (3 if precision == "split" else 1)
+
+
+def with_tensor_bound(hbm, flops, ms):
+    """The HBM roofline `hbm` and the tensor one (flops per launch over `ms`): the binding
+    bound (the larger fraction) leads, the other is kept under its own name."""
+    peak, kind = measured_tensor_peak()
+    ach = flops / (ms / 1e3) / 1e12
+    ten = {"bound": "tensor", "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s",
+           "frac": round(ach / peak, 4), "peak_kind": kind, "algorithmic_flops_per_launch": flops}
+    if ten["frac"] <= hbm["frac"]:
+        return dict(hbm, tensor=ten)
+    other = {k: v for k, v in hbm.items() if k not in ("traffic",)}
+    return dict(ten, traffic=hbm.get("traffic"), hbm=other)
 
 
 def xspec_traffic_per_launch(workload_name, precision, kernel="k_xspec_tc"):
@@ -598,9 +631,10 @@ def run_forms(args, ctx, stream, flush, y, yd, phi, psi, ldo, rows, cols, checks
         else:
             xb = (4.0 if kw.get("output_bf16") else 8.0) * outs + 1.0 * n * rowlen_elems(m, prec) * 2
             ach = xb / (xms / 1e3) / 1e9
-            d["roofline"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak,
-                             "unit": "GB/s", "frac": round(ach / peak, 4),
-                             "algorithmic_bytes_per_launch": xb}
+            d["roofline"] = with_tensor_bound(
+                {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                 "frac": round(ach / peak, 4), "algorithmic_bytes_per_launch": xb},
+                tensor_flops(m, prec, n * (n + 1) / 2), xms)
         r, c = sample_block(n, upper)
         checks[name] = [(y, None, r, c, 0.0, gather(o[0], o[1], r, c))]
         return d
@@ -644,9 +678,11 @@ def run_forms(args, ctx, stream, flush, y, yd, phi, psi, ldo, rows, cols, checks
             d["prep_ms"] = round(statistics.mean(t["prep_ms"]), 4)
             xb = batch_bytes(spec, "split")
             ach = xb / (xms / 1e3) / 1e9
-            d["roofline"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak,
-                             "unit": "GB/s", "frac": round(ach / peak, 4),
-                             "algorithmic_bytes_per_launch": xb}
+            fl = sum(tensor_flops(p.m, "split", p.n1 * (p.n1 + 1) / 2 if p.homo else p.n1 * p.n2)
+                     for p in spec.problems)
+            d["roofline"] = with_tensor_bound(
+                {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                 "frac": round(ach / peak, 4), "algorithmic_bytes_per_launch": xb}, fl, xms)
         checks[name] = c5_checks()
         return d
 
@@ -695,13 +731,16 @@ def run_ours(args, world, rank, local, pg):
         # Phi and Psi stored (the upper triangle only: n (n + 1) / 2 pairs), the homo
         # problem's one operand row set read once
         stored = n * (n + 1) / 2 if upper else n * n
+        pairs = n * (n + 1) / 2  # the unique pairs of a homo map: the tensor-core work
         if strong:
             # this rank's part of the mirrored tile list: its blocks and mirrored blocks
             tiles = pkg.corr2d_plan_part(n, n, True, 0, rank, world)
-            stored = 0.0
+            stored = pairs = 0.0
             for ti, tj in tiles:
-                area = min(128, n - 128 * ti) * min(128, n - 128 * tj)
+                h = min(128, n - 128 * ti)
+                area = h * min(128, n - 128 * tj)
                 stored += area * (1 if (upper or ti == tj) else 2)
+                pairs += h * (h + 1) / 2 if ti == tj else area
             scaling = "strong"
             parallelism = (f"strong: one problem split by output tiles over {world} GPUs "
                            f"(corr2d_compute_part, balanced parts of the mirrored tile list; "
@@ -715,6 +754,7 @@ def run_ours(args, world, rank, local, pg):
                 ctx.compute(yd, precision=args.precision, out=(phi, psi), upper_triangle=upper,
                             output_bf16=obf)
         xbytes = (4.0 if obf else 8.0) * stored + 1.0 * n * rowlen_elems(m, args.precision) * 2
+        tflops = tensor_flops(m, args.precision, pairs)
         if upper:
             desc["workload"] += " upper triangle"
             desc["upper_triangle"] = True
@@ -735,6 +775,7 @@ def run_ours(args, world, rank, local, pg):
             ctx.compute(a, b, precision=args.precision, alpha=raw.alpha, out=(phi, psi))
         launches_per_step = 4  # 2 x resampling (axis check inside), DFT, cross-spectrum
         xbytes = 8.0 * n1 * n2 + 2.0 * (n1 + n2) * rowlen_elems(128, args.precision)
+        tflops = tensor_flops(128, args.precision, n1 * n2)
         y = raw.y1
     else:
         spec = inputs
@@ -774,6 +815,9 @@ def run_ours(args, world, rank, local, pg):
             def step():
                 plan.run()
         xbytes = batch_bytes(spec, args.precision)
+        tflops = sum(tensor_flops(p.m, args.precision,
+                                  p.n1 * (p.n1 + 1) / 2 if p.homo else p.n1 * p.n2)
+                     for p in spec.problems)
         desc["batched"] = not (args.no_batch or args.precision == "fp32")
         y = None
 
@@ -826,6 +870,21 @@ def run_ours(args, world, rank, local, pg):
             ss = store_stream_same_size_gbs(device, 8.0 * outputs, flush)
             roofline.update({"store_stream_same_size_gbs": ss,
                              "frac_of_same_size_store_stream": round(achieved / ss, 4)})
+        # the tensor roofline beside it; where it binds (the upper triangle: half the stores
+        # for the same products) it leads and the HBM figures move under "hbm"
+        tpeak, tkind = measured_tensor_peak()
+        tach = tflops / (x_mean / 1e3) / 1e12
+        ten = {"bound": "tensor", "achieved": round(tach, 1), "peak": tpeak, "unit": "TFLOP/s",
+               "frac": round(tach / tpeak, 4), "peak_kind": tkind,
+               "algorithmic_flops_per_launch": tflops}
+        if ten["frac"] > roofline["frac"]:
+            moved = ("bound", "achieved", "peak", "unit", "frac", "peak_kind",
+                     "algorithmic_bytes_per_launch", "store_stream_gbs", "frac_of_store_stream",
+                     "store_stream_same_size_gbs", "frac_of_same_size_store_stream")
+            roofline["hbm"] = {k: roofline.pop(k) for k in moved if k in roofline}
+            roofline.update(ten)
+        else:
+            roofline["tensor"] = ten
     if args.precision == "fp32":
         fp32_peak = ctx.fp32_peak_tflops()
         kp1 = (desc.get("m", 2) - 1) // 2 + 1

@@ -402,11 +402,13 @@ corr2d_status corr2d_get_timings(corr2d_ctx* ctx, float* prep_ms, float* xspec_m
  * kernel the last corr2d_compute / corr2d_batch call on this context launched
  * (CORR2D_XSPEC_* below), and how many CTA pairs the device runs at once (0:
  * the CTA-pair kernel is unavailable).  Either output may be NULL (host
- * ints otherwise); EINVAL for a NULL context.  The tuner times the single-CTA kernel's tile shapes and
- * orders; the environment variable CORR2D_XSPEC=pair makes it use the CTA-pair
- * kernel instead, =ta the kernel that holds the stack-1 operand in TMEM (up to
- * 8 frequency chunks: split m <= 256, BF16 m <= 512; the single-CTA kernel
- * beyond), =any lets it time every kind, =single is the default. */
+ * ints otherwise); EINVAL for a NULL context.  The tuner times the single-CTA
+ * kernel's tile shapes and orders, and for upper-triangle output of a homo
+ * problem also the kernel that holds the stack-1 operand in TMEM (up to 8
+ * frequency chunks: split m <= 256, BF16 m <= 512); the environment variable
+ * CORR2D_XSPEC=pair makes it use the CTA-pair kernel instead, =ta the TMEM
+ * one (the single-CTA kernel beyond 8 chunks), =any lets it time every kind,
+ * =single holds it to the single-CTA kernel. */
 enum { CORR2D_XSPEC_NONE = 0, CORR2D_XSPEC_TC = 1, CORR2D_XSPEC_TC_PAIR = 2,
        CORR2D_XSPEC_FP32 = 3, CORR2D_XSPEC_TC_TA = 4 };
 corr2d_status corr2d_get_kernel_info(corr2d_ctx* ctx, int* last_xspec, int* pair_clusters);

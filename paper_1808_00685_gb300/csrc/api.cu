@@ -1042,16 +1042,22 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
   const bool homo = (y2 == nullptr);
   const int n2e = homo ? n1 : n2;
   // Cross-spectrum kernels the tuner may choose from: the single-CTA kernel by
-  // default; CORR2D_XSPEC=pair selects the CTA-pair kernel, =any lets the
-  // tuner time both (the pair kernel measured slower on every workload tried).
+  // default, with the TMEM-operand kernel beside it for upper-triangle output
+  // (half the stores for the same products: there the operand side binds, and
+  // halving the tensor cores' shared-memory operand reads measured 3 % faster
+  // on homo m = 256 n = 32768); CORR2D_XSPEC=pair selects the CTA-pair kernel,
+  // =ta the TMEM-operand one, =any lets the tuner time all three (the pair
+  // kernel measured slower on every workload tried).
   const char* xk = getenv("CORR2D_XSPEC");
+  const bool any = xk && strcmp(xk, "any") == 0;
   // (the CTA-pair and TMEM-operand kernels store FP32 only)
   const bool obf = (p.flags & CORR2D_FLAG_OUTPUT_BF16) != 0;
-  const bool want_pair = !obf && xk && (strcmp(xk, "pair") == 0 || strcmp(xk, "any") == 0);
-  const bool want_ta = xk && (strcmp(xk, "ta") == 0 || strcmp(xk, "any") == 0) &&
+  const bool want_pair = !obf && xk && (strcmp(xk, "pair") == 0 || any);
+  const bool upper_ta = !xk && (p.flags & CORR2D_FLAG_UPPER_TRIANGLE) && homo;
+  const bool want_ta = (upper_ta || (xk && (strcmp(xk, "ta") == 0 || any))) &&
                        chunks_for(m, p.precision == CORR2D_PREC_SPLIT ? 2 : 1) <= TA_MAX_CHUNKS &&
                        !(p.flags & CORR2D_FLAG_HILBERT) && !obf;
-  const bool want_single = (!want_pair && !want_ta) || strcmp(xk, "any") == 0 ||
+  const bool want_single = !xk || (!want_pair && !want_ta) || any ||
                            (want_pair && ctx->pair_clusters == 0);
   const int flag_bits = (int)(p.flags & (CORR2D_FLAG_NO_MIRROR | CORR2D_FLAG_EXACT_SYMMETRY |
                                          CORR2D_FLAG_HILBERT | CORR2D_FLAG_UPPER_TRIANGLE |

@@ -47,3 +47,24 @@ def test_cpu_baseline_leg_reports_the_error_of_what_it_is_given():
     e = errors["planted"]
     assert e["max_abs_phi"] == pytest.approx(1e-3 * e["largest_magnitude"], rel=1e-9)
     assert e["rel_err_phi"] > 0 and e["rel_err_psi"] == 0.0
+
+
+def test_tensor_flops_count_the_split_products_and_the_binding_bound_leads():
+    # homo m = 256 (K' = 128) over the 32768 x 32768 map's unique pairs, three products each
+    pairs = 32768 * 32769 / 2
+    fl = bench.tensor_flops(256, "split", pairs)
+    assert fl == 3 * 8 * 128 * pairs
+    assert bench.tensor_flops(256, "bf16", pairs) == fl / 3
+    assert bench.tensor_flops(2, "split", 1) == 24  # m = 2: K' = 1 (omega = 0 only)
+    peak, _ = bench.measured_tensor_peak()
+    # the full map's kernel time: HBM binds and leads, the tensor figures sit beside it
+    hbm = {"bound": "hbm", "achieved": 6450.0, "peak": 6792.1, "unit": "GB/s", "frac": 0.95,
+           "algorithmic_bytes_per_launch": 8.6e9}
+    r = bench.with_tensor_bound(hbm, fl, 1.334)
+    assert r["bound"] == "hbm" and r["tensor"]["bound"] == "tensor"
+    assert r["tensor"]["achieved"] == pytest.approx(fl / 1.334e-3 / 1e12, abs=0.05)
+    # half the stores for the same products: the tensor bound binds and leads
+    hbm_u = dict(hbm, achieved=3785.0, frac=0.557)
+    r = bench.with_tensor_bound(hbm_u, fl, 1.133)
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s" and r["hbm"]["frac"] == 0.557
+    assert r["frac"] == pytest.approx(fl / 1.133e-3 / 1e12 / peak, abs=1e-4)
