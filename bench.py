@@ -63,7 +63,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["c4", "c2", "c3", "c5"], default="c4")
     ap.add_argument("--precision", choices=["split", "bf16", "fp32"], default="split")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
@@ -946,6 +946,7 @@ def run_ours(args, world, rank, local, pg):
         e2e = {"value": world * outputs / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": d2h_b,
                "api": "corr2d_compute_host", "ms_per_step": round(e2e_s * 1e3, 2),
+               "ms_each_step": [round(t * 1e3, 2) for t in times],
                "link": {**link, "numa_node": node,
                         "pinned_on": "GPU's NUMA node" if cpus else "default placement",
                         "output_copy_ms": round(out_ms, 2),

@@ -544,6 +544,30 @@ def test_host_buffer_entry_point(ctx):
     check(phi.double().numpy(), psi.double().numpy(), ophi, opsi, 1e-5, "host buffers homo")
 
 
+def test_host_buffer_entry_point_over_several_slabs(ctx):
+    """The host path streams the output through two device slab buffers of up to 256 MB
+    (here 8 tile rows of 32768 columns each), each slab's copies running while the next
+    slab is computed into the other buffer: three slabs, the last one partial, held to the
+    oracle on rows at the slab edges, then a second call into the same pinned buffers gives
+    the same bits."""
+    m, n1, n2 = 24, 2500, 32768
+    y1 = workloads.random_stack(m, n1, seed=31)
+    y2 = workloads.random_stack(m, n2, seed=32, offset=-1.0)
+    t1, t2 = torch.from_numpy(y1).pin_memory(), torch.from_numpy(y2).pin_memory()
+    phi = torch.empty((n1, n2), dtype=torch.float32, pin_memory=True)
+    psi = torch.empty((n1, n2), dtype=torch.float32, pin_memory=True)
+    ctx.compute_host(t1, t2, out=(phi, psi))
+    rows = np.array([0, 1, 1023, 1024, 1025, 2047, 2048, 2049, 2498, 2499])
+    ophi, opsi, _, _ = oracle.corr2d(y1, y2, rows=rows, nthreads=oracle.max_threads())
+    a, b = phi.numpy()[rows].astype(np.float64), psi.numpy()[rows].astype(np.float64)
+    check(a, b, ophi, opsi, 1e-5, "host buffers, three slabs")
+    first = (phi.clone(), psi.clone())
+    phi.fill_(float("nan"))
+    psi.fill_(float("nan"))
+    ctx.compute_host(t1, t2, out=(phi, psi))
+    assert torch.equal(phi, first[0]) and torch.equal(psi, first[1])
+
+
 def test_preprocess_perturbation_bit_exact_and_feeds_compute(ctx):
     """Sec. 4.2 perturbation-axis interpolation: uneven Time -> N equidistant steps,
     bit-exact against the oracle, then the correlation of the resampled stack."""
