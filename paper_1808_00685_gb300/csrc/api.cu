@@ -1053,7 +1053,8 @@ static corr2d_status choose_tiles(corr2d_ctx* ctx, int m, int n1, const float* y
   // (the CTA-pair and TMEM-operand kernels store FP32 only)
   const bool obf = (p.flags & CORR2D_FLAG_OUTPUT_BF16) != 0;
   const bool want_pair = !obf && xk && (strcmp(xk, "pair") == 0 || any);
-  const bool upper_ta = !xk && (p.flags & CORR2D_FLAG_UPPER_TRIANGLE) && homo;
+  const bool upper_ta = !xk && homo && (p.flags & CORR2D_FLAG_UPPER_TRIANGLE) &&
+                        !(p.flags & CORR2D_FLAG_NO_MIRROR);  // (no mirror: a full map)
   const bool want_ta = (upper_ta || (xk && (strcmp(xk, "ta") == 0 || any))) &&
                        chunks_for(m, p.precision == CORR2D_PREC_SPLIT ? 2 : 1) <= TA_MAX_CHUNKS &&
                        !(p.flags & CORR2D_FLAG_HILBERT) && !obf;
